@@ -1,0 +1,158 @@
+/*
+ * kpm.h - C ABI of the GB300 KPM observable engine for the renormalised
+ * mean-field (Gutzwiller) vortex solver of arXiv:2212.05685.
+ *
+ * Every entry point returns an int status (KPM_OK = 0, negative on error; see
+ * kpm_strerror) and never throws or aborts across the ABI.  Array arguments
+ * are plain pointers owned by the caller; unless stated otherwise they must be
+ * device pointers of the context's GPU, 16-byte aligned, and are used
+ * asynchronously on `stream` (a cudaStream_t passed as void*, NULL = the
+ * legacy default stream).  The context owns only scratch memory (recursion
+ * slabs, accumulators, CUDA graphs).
+ *
+ * Lattice and array layouts (N = nx*ny sites, site i = x + nx*y, periodic):
+ *
+ *   forward bonds d = 0..3 : i -> i + (+x, +y, +x+y, +x-y)
+ *   ordered nn pairs e = 0..3 : i -> i + (+x, +y, -x, -y)
+ *
+ *   order parameters ("params"/"obs", float64, 26*N):
+ *     [0, 2N)     n[s][i]            s = 0 up, 1 down          (Eq. delta, mz)
+ *     [2N, 18N)   chi[s][d][i]       complex, interleaved       (Eq. chi)
+ *                 chi_{i,i+d,s} = <c^dag_{i s} c_{i+d, s}>
+ *     [18N, 26N)  F[e][i]            complex, interleaved       (Eq. pairing)
+ *                 F_{i,i+e} = <c_{i up} c_{i+e, dn}>; the paper's
+ *                 Delta_{ij up} = F_ij and Delta_{ij dn} = F_ji
+ *
+ *   effective fields ("fields", float64, 26*N, same layout):
+ *     eps[s][i] = dW/dn_{i s},  T[s][d][i] = dW/dchi_{i,i+d,s},
+ *     D[e][i] = dW/dF*_{i,i+e}                           (Eqs. Tij, Dij, mu_i)
+ *
+ *   Nambu matrix (App. B, d_i = (c_{i up}, c^dag_{i dn}), row I = 2i + alpha):
+ *     h[(i,0),(i,0)] = eps_{i up},  h[(i,1),(i,1)] = -eps_{i dn},
+ *     h[(i,0),(j,0)] = T_{ij up},   h[(i,1),(j,1)] = -conj(T_{ij dn}),
+ *     h[(i,0),(j,1)] = -D_{ij},     plus Hermitian conjugates.
+ *
+ *   Peierls phases ("phi", float64, 4*N): phi[d][i] on the forward bonds,
+ *     t_{i,i+d} = t e^{i phi} (d < 2) or t' e^{i phi} (d >= 2)  (Sec. II).
+ */
+#ifndef KPM_H
+#define KPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KPM_OK 0
+#define KPM_EINVAL (-1)      /* bad size, null pointer, misaligned or host pointer where a device one is required */
+#define KPM_ENOMEM (-2)      /* scratch allocation failed */
+#define KPM_ECUDA (-3)       /* a CUDA call failed; kpm_last_error() has the CUDA message */
+#define KPM_ENONFINITE (-4)  /* NaN or Inf in an output */
+#define KPM_ETIMEDOUT (-5)   /* a bounded device wait expired (reserved; no kernel of this library spins) */
+#define KPM_ENOTCONV (-6)    /* rmft_iterate reached n_iter without meeting tol (only if asked to report it) */
+
+#define KPM_FP64 0
+#define KPM_FP32 1
+
+typedef struct kpm_ctx kpm_ctx;
+
+/* t-t'-J model on an nx x ny torus threaded by `flux` quanta hc/e
+ * (B = 2 Phi0 / (nx ny) per quantum, App. C).  nx, ny >= 2. */
+typedef struct {
+  int32_t nx, ny;
+  int32_t flux;
+  int32_t gutzwiller;   /* 1: Gutzwiller factors of App. A; 0: all g = 1 */
+  double t, tp, J;      /* nn hopping, nnn hopping, exchange (paper: 1, -0.3, 0.3) */
+} kpm_model;
+
+/* Chebyshev expansion options (App. B). */
+typedef struct {
+  int32_t M;            /* number of moments, M >= 1 (paper: 1000-2000) */
+  int32_t precision;    /* KPM_FP64: FP64 recursion; KPM_FP32: FP32 vectors and
+                           coefficients, FP64 moment sums and everything else */
+  int32_t block_width;  /* unit start vectors per slab; 0 = as many as fit the
+                           context's scratch budget (kpm_set_scratch_budget) */
+  int32_t cols_per_block; /* columns per CTA in the recursion kernel; 0 = default */
+  double margin;        /* spectral half-width margin of the Gershgorin rescale (0.01) */
+} kpm_opts;
+
+/* Self-consistency options (the paper's iteration, readings R1/R2). */
+typedef struct {
+  double n_target;      /* electrons per site, 1 - delta */
+  double alpha;         /* mixing of chi and F (0.5) */
+  double alpha_n;       /* mixing of the densities (0.05) */
+  double eta;           /* gain of the chemical-potential feedback (0.5) */
+  double tol;           /* converged when max |p_new - p| and |<n> - n_target| < tol */
+  int32_t paramagnetic; /* 1: keep n_up = n_dn (m = 0 sector) */
+  int32_t reserved;
+} kpm_rmft_opts;
+
+/* Per-call results of rmft_iterate (host struct, filled before return). */
+typedef struct {
+  double residual;      /* max |p_new - p| of the last iteration */
+  double density_error; /* <n_new> - n_target of the last iteration */
+  double mu;            /* Lagrange multiplier mu = mu_eff + <dW/dn|_{mu=0}> */
+  double omega;         /* KPM grand potential Omega_M = a tr G_M(h~) of the last pass */
+  double a, b;          /* spectral rescale h~ = (h - b)/a of the last pass */
+  int32_t iterations;   /* iterations performed by this call */
+  int32_t converged;    /* 1 if the last iteration met tol */
+} kpm_rmft_stats;
+
+/* Create a context on CUDA device `device`.  Allocates nothing yet. */
+int kpm_create(kpm_ctx** out, int device);
+/* Free the context and all its scratch.  Synchronises the device. */
+int kpm_destroy(kpm_ctx* ctx);
+/* Upper bound (bytes) on recursion-slab scratch; default 24 GiB. */
+int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes);
+const char* kpm_strerror(int status);
+/* Last error message of this context (static storage of the context). */
+const char* kpm_last_error(const kpm_ctx* ctx);
+
+/* Peierls phases of the Landau gauge A = B(0, x) (Sec. II, App. C), with the
+ * magnetic-translation phase 2 pi flux y'/ny on bonds crossing the x boundary
+ * and straight-line integrals on next-nearest-neighbour bonds.
+ * phi: device, 4*N doubles, written. */
+int kpm_peierls_phases(kpm_ctx* ctx, const kpm_model* model, double* phi, void* stream);
+
+/* Effective fields of the renormalised functional (App. A, Eqs. Tij, Dij,
+ * mu_i): fields = dW/d(params) at chemical potential `mu`.
+ * phi: device 4*N; params: device 26*N; fields: device 26*N (written);
+ * w_out: device double or NULL; written with W = <H_renorm> - mu sum_i n_i
+ * (the constant mu N_e of App. A omitted). */
+int kpm_build_H(kpm_ctx* ctx, const kpm_model* model, const double* phi,
+                const double* params, double mu, double* fields, double* w_out,
+                void* stream);
+
+/* Gershgorin bounds of the Nambu matrix (App. B "shifting and rescaling"):
+ * ab[0] = a = (1 + margin)(Emax - Emin)/2, ab[1] = b = (Emax + Emin)/2, with
+ * Emax/Emin over rows of h_II +- sum of the moduli of the 12 off-diagonal
+ * stencil entries (a = 1 when Emax = Emin).  fields: device; ab: device, 2 doubles. */
+int kpm_bounds(kpm_ctx* ctx, const kpm_model* model, const double* fields,
+               double margin, double* ab, void* stream);
+
+/* One KPM pass (App. B, Eqs. rho_KPM, F_KPM, alpha) over all D = 2N unit
+ * start vectors: obs = order parameters read off F_M(h~)^T = rho with
+ * F_M = sum_m (2 - delta_m0) g_m c_m T_m the Jackson-damped T = 0 step at BdG
+ * energy 0; omega = a tr G_M(h~) with G_M the damped series of min(x - x0, 0).
+ * fields, ab: device (ab as written by kpm_bounds).  obs: device 26*N,
+ * written.  omega: device double or NULL. */
+int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
+                    const double* fields, const double* ab, double* obs,
+                    double* omega, void* stream);
+
+/* Up to n_iter self-consistency iterations of App. A: fields from params,
+ * bounds, one KPM pass, then the mixing update (readings R1, R2).  params
+ * (26*N doubles) and mu_eff (1 double) are read and updated in place; they may
+ * be device pointers or host pointers (host buffers are staged through the
+ * stream, copies included in the call).  phi: device or host, 4*N.
+ * Blocks until the iterations are done (the host reads the residual after
+ * each iteration).  Returns KPM_ENONFINITE on NaN/Inf. */
+int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
+                 const kpm_rmft_opts* ropts, const double* phi, double* params,
+                 double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPM_H */

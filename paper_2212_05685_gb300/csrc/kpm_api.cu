@@ -1,0 +1,494 @@
+// C ABI of libkpm.so: context and scratch management, argument checks, the
+// ordering of one KPM pass (coefficients, rescaled stencil table, slab
+// recursions, assembly) and of one self-consistency iteration, captured once
+// into a CUDA graph and replayed.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include <algorithm>
+#include <string>
+
+#include "kpm_internal.cuh"
+
+using namespace kpm;
+
+struct kpm_ctx {
+  int device = 0;
+  cudaStream_t cap = nullptr;  // capture stream of the iteration graph
+  std::string err;
+  uint64_t budget = 24ull << 30;
+
+  // scratch (owned)
+  void* slab[2] = {nullptr, nullptr};
+  size_t slab_bytes = 0;
+  double2* acc = nullptr;
+  size_t acc_bytes = 0;
+  void* table = nullptr;
+  size_t table_bytes = 0;
+  double* am = nullptr;
+  double* ao = nullptr;
+  size_t coef_n = 0;
+  double* red = nullptr;        // reduction partials
+  double* fields = nullptr;     // 26 N
+  double* obs = nullptr;        // 26 N
+  double* wsite = nullptr;      // N
+  double* dparams = nullptr;    // 26 N (host-pointer staging)
+  double* dphi = nullptr;       // 4 N
+  size_t site_n = 0;
+  double* misc = nullptr;       // [0..1] ab, [2] mu, [3] omega, [4..5] stats, [6] mean, [7] mu_eff, [8] W
+  double* host_misc = nullptr;  // pinned mirror of misc
+
+  // cached iteration graph
+  cudaGraphExec_t graph = nullptr;
+  struct Key {
+    kpm_model m;
+    kpm_opts o;
+    kpm_rmft_opts r;
+    const double* phi;
+    double* params;
+    double* mu_eff;
+  } key;
+  bool key_valid = false;
+};
+
+namespace {
+
+int fail(kpm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(kpm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, KPM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define KPM_CU(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_model(kpm_ctx* ctx, const kpm_model* m) {
+  if (!m) return fail(ctx, KPM_EINVAL, "model is null");
+  if (m->nx < 2 || m->ny < 2) return fail(ctx, KPM_EINVAL, "lattice needs nx, ny >= 2");
+  if ((int64_t)m->nx * m->ny > (1 << 26)) return fail(ctx, KPM_EINVAL, "lattice too large");
+  return KPM_OK;
+}
+
+int check_dev(kpm_ctx* ctx, const void* p, const char* name) {
+  if (!p) return fail(ctx, KPM_EINVAL, std::string(name) + " is null");
+  if (((uintptr_t)p) % 8) return fail(ctx, KPM_EINVAL, std::string(name) + " is not 8-byte aligned");
+  if (!is_device_ptr(p)) return fail(ctx, KPM_EINVAL, std::string(name) + " is not a device pointer");
+  return KPM_OK;
+}
+
+template <typename T>
+int ensure(kpm_ctx* ctx, T** p, size_t* have, size_t need_bytes) {
+  if (*p && *have >= need_bytes) return KPM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc((void**)p, need_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, KPM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  *have = need_bytes;
+  return KPM_OK;
+}
+
+void drop_graph(kpm_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  ctx->key_valid = false;
+}
+
+int ensure_site_scratch(kpm_ctx* ctx, int N) {
+  if (ctx->site_n >= (size_t)N && ctx->fields) return KPM_OK;
+  drop_graph(ctx);
+  double** bufs[5] = {&ctx->fields, &ctx->obs, &ctx->wsite, &ctx->dparams, &ctx->dphi};
+  const size_t sizes[5] = {26, 26, 1, 26, 4};
+  for (int k = 0; k < 5; ++k) {
+    if (*bufs[k]) cudaFree(*bufs[k]);
+    *bufs[k] = nullptr;
+    if (cudaMalloc((void**)bufs[k], sizes[k] * (size_t)N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->site_n = 0;
+      return fail(ctx, KPM_ENOMEM, "cudaMalloc of per-site scratch failed");
+    }
+  }
+  ctx->site_n = N;
+  return KPM_OK;
+}
+
+struct PassPlan {
+  ChebPlan cheb;
+  int64_t width;  // unit columns per slab
+  size_t elem;    // bytes per complex
+};
+
+int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp) {
+  if (!o) return fail(ctx, KPM_EINVAL, "opts is null");
+  if (o->M < 1) return fail(ctx, KPM_EINVAL, "M must be >= 1");
+  if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return fail(ctx, KPM_EINVAL, "unknown precision");
+  if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
+  const int64_t D = 2 * (int64_t)m->nx * m->ny;
+  pp->elem = o->precision == KPM_FP32 ? 8 : 16;
+  int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, D) : D;
+  if (o->block_width == 0) {
+    const int64_t fit = (int64_t)(ctx->budget / (2 * (uint64_t)D * pp->elem));
+    width = std::min<int64_t>(width, std::max<int64_t>(fit, 1));
+  }
+  pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
+  if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
+  pp->width = width;
+  return KPM_OK;
+}
+
+int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp) {
+  const int64_t D = pp.cheb.D;
+  const size_t slab = (size_t)D * pp.cheb.ldv * pp.elem;
+  int r;
+  if (ctx->slab_bytes < slab) {
+    drop_graph(ctx);
+    for (int k = 0; k < 2; ++k) {
+      if (ctx->slab[k]) cudaFree(ctx->slab[k]);
+      ctx->slab[k] = nullptr;
+    }
+    ctx->slab_bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+      if (cudaMalloc(&ctx->slab[k], slab) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KPM_ENOMEM, "cudaMalloc of the recursion slabs failed");
+      }
+    }
+    ctx->slab_bytes = slab;
+  }
+  const size_t accb = (size_t)D * kSlots * sizeof(double2);
+  if (ctx->acc_bytes < accb) drop_graph(ctx);
+  if ((r = ensure(ctx, &ctx->acc, &ctx->acc_bytes, accb))) return r;
+  const size_t tb = (size_t)m->nx * m->ny * kCoef * pp.elem;
+  if (ctx->table_bytes < tb) drop_graph(ctx);
+  if ((r = ensure(ctx, &ctx->table, &ctx->table_bytes, tb))) return r;
+  if (ctx->coef_n < (size_t)o->M) {
+    drop_graph(ctx);
+    if (ctx->am) cudaFree(ctx->am);
+    if (ctx->ao) cudaFree(ctx->ao);
+    ctx->am = ctx->ao = nullptr;
+    ctx->coef_n = 0;
+    if (cudaMalloc(&ctx->am, o->M * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->ao, o->M * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, KPM_ENOMEM, "cudaMalloc of coefficients failed");
+    }
+    ctx->coef_n = o->M;
+  }
+  if (!ctx->red) {
+    if (cudaMalloc(&ctx->red, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, KPM_ENOMEM, "cudaMalloc of reduction scratch failed");
+    }
+  }
+  cudaError_t e = cheb_prepare(pp.cheb, o->precision);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cheb_prepare");
+  return KPM_OK;
+}
+
+// enqueue one KPM pass: fields + ab (device) -> obs, omega
+int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
+                 const double* ab, double* obs, double* omega, cudaStream_t s) {
+  const ChebPlan& p = pp.cheb;
+  const int M = o->M;
+  const int prec = o->precision;
+  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
+  if (prec == KPM_FP32)
+    KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
+  else
+    KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
+  void* A = ctx->slab[0];
+  void* B = ctx->slab[1];
+  for (int64_t s0 = 0; s0 < p.D; s0 += pp.width) {
+    KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, ctx->am, ctx->ao, s));
+    if (M >= 2) KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
+    for (int mm = 1; mm <= M - 2; ++mm) {
+      const void* cur = (mm & 1) ? B : A;
+      void* out = (mm & 1) ? A : B;
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, ctx->acc, ctx->am, ctx->ao, mm, 1, s));
+    }
+    if (M >= 2) {
+      const void* last = ((M - 1) & 1) ? B : A;
+      KPM_CU(launch_cheb_gather(p, prec, last, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
+    }
+  }
+  KPM_CU(launch_assemble(m->nx * m->ny, ctx->acc, ab, obs, omega, ctx->red, s));
+  return KPM_OK;
+}
+
+int ensure_misc(kpm_ctx* ctx) {
+  if (ctx->misc) return KPM_OK;
+  if (cudaMalloc(&ctx->misc, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  if (cudaMallocHost(&ctx->host_misc, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMallocHost failed");
+  }
+  cudaMemset(ctx->misc, 0, 16 * sizeof(double));
+  return KPM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool same_key(const kpm_ctx::Key& a, const kpm_ctx::Key& b) { return memcmp(&a, &b, sizeof(a)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* kpm_strerror(int status) {
+  switch (status) {
+    case KPM_OK: return "ok";
+    case KPM_EINVAL: return "invalid argument";
+    case KPM_ENOMEM: return "out of device memory";
+    case KPM_ECUDA: return "CUDA error";
+    case KPM_ENONFINITE: return "non-finite value in an output";
+    case KPM_ETIMEDOUT: return "bounded device wait expired";
+    case KPM_ENOTCONV: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+const char* kpm_last_error(const kpm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int kpm_create(kpm_ctx** out, int device) {
+  if (!out) return KPM_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return KPM_EINVAL;
+  }
+  kpm_ctx* ctx = new (std::nothrow) kpm_ctx();
+  if (!ctx) return KPM_ENOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return KPM_ECUDA;
+  }
+  *out = ctx;
+  return KPM_OK;
+}
+
+int kpm_destroy(kpm_ctx* ctx) {
+  if (!ctx) return KPM_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  drop_graph(ctx);
+  for (void* p : {ctx->slab[0], ctx->slab[1], (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
+                  (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
+                  (void*)ctx->dphi, (void*)ctx->misc})
+    if (p) cudaFree(p);
+  if (ctx->host_misc) cudaFreeHost(ctx->host_misc);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  delete ctx;
+  return KPM_OK;
+}
+
+int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes) {
+  if (!ctx || bytes < (1u << 20)) return KPM_EINVAL;
+  ctx->budget = bytes;
+  return KPM_OK;
+}
+
+int kpm_peierls_phases(kpm_ctx* ctx, const kpm_model* model, double* phi, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, phi, "phi"))) return r;
+  DeviceGuard g(ctx->device);
+  KPM_CU(launch_peierls(*model, phi, (cudaStream_t)stream));
+  return KPM_OK;
+}
+
+int kpm_build_H(kpm_ctx* ctx, const kpm_model* model, const double* phi, const double* params, double mu,
+                double* fields, double* w_out, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, phi, "phi")) || (r = check_dev(ctx, params, "params")) ||
+      (r = check_dev(ctx, fields, "fields")))
+    return r;
+  if (w_out && (r = check_dev(ctx, w_out, "w_out"))) return r;
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  if ((r = ensure_site_scratch(ctx, N))) return r;
+  if (!ctx->red && cudaMalloc(&ctx->red, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  KPM_CU(launch_fields(*model, phi, params, mu, fields, ctx->wsite, s));
+  if (w_out) KPM_CU(launch_sum(ctx->wsite, N, w_out, ctx->red, s));
+  return KPM_OK;
+}
+
+int kpm_bounds(kpm_ctx* ctx, const kpm_model* model, const double* fields, double margin, double* ab,
+               void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, fields, "fields")) || (r = check_dev(ctx, ab, "ab"))) return r;
+  if (!(margin >= 0.0)) return fail(ctx, KPM_EINVAL, "margin must be >= 0");
+  DeviceGuard g(ctx->device);
+  if (!ctx->red && cudaMalloc(&ctx->red, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  KPM_CU(launch_gershgorin(*model, fields, margin, ab, ctx->red, (cudaStream_t)stream));
+  return KPM_OK;
+}
+
+int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
+                    const double* ab, double* obs, double* omega, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, fields, "fields")) || (r = check_dev(ctx, ab, "ab")) || (r = check_dev(ctx, obs, "obs")))
+    return r;
+  if (omega && (r = check_dev(ctx, omega, "omega"))) return r;
+  DeviceGuard g(ctx->device);
+  PassPlan pp;
+  if ((r = plan_pass(ctx, model, opts, &pp))) return r;
+  if ((r = ensure_pass_scratch(ctx, model, opts, pp))) return r;
+  return enqueue_pass(ctx, model, opts, pp, fields, ab, obs, omega, (cudaStream_t)stream);
+}
+
+int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const kpm_rmft_opts* ropts,
+                 const double* phi, double* params, double* mu_eff, int n_iter, kpm_rmft_stats* stats,
+                 void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if (!ropts || !phi || !params || !mu_eff) return fail(ctx, KPM_EINVAL, "null argument");
+  if (n_iter < 0) return fail(ctx, KPM_EINVAL, "n_iter must be >= 0");
+  if (!(ropts->alpha > 0.0 && ropts->alpha <= 1.0 && ropts->alpha_n > 0.0 && ropts->alpha_n <= 1.0))
+    return fail(ctx, KPM_EINVAL, "mixing must lie in (0, 1]");
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  cudaStream_t s = (cudaStream_t)stream;
+  PassPlan pp;
+  if ((r = plan_pass(ctx, model, opts, &pp))) return r;
+  if ((r = ensure_site_scratch(ctx, N))) return r;
+  if ((r = ensure_pass_scratch(ctx, model, opts, pp))) return r;
+  if ((r = ensure_misc(ctx))) return r;
+
+  // host or device buffers: stage host ones through the context
+  const bool params_dev = is_device_ptr(params);
+  const bool phi_dev = is_device_ptr(phi);
+  const bool mu_dev = is_device_ptr(mu_eff);
+  double* dpar = params_dev ? params : ctx->dparams;
+  const double* dphi = phi_dev ? phi : ctx->dphi;
+  double* dmu = mu_dev ? mu_eff : ctx->misc + 7;
+  if (!params_dev) KPM_CU(cudaMemcpyAsync(dpar, params, 26 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (!phi_dev) KPM_CU(cudaMemcpyAsync((void*)dphi, phi, 4 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (!mu_dev) KPM_CU(cudaMemcpyAsync(dmu, mu_eff, sizeof(double), cudaMemcpyHostToDevice, s));
+
+  kpm_ctx::Key key;
+  memset(&key, 0, sizeof(key));
+  key.m = *model;
+  key.o = *opts;
+  key.r = *ropts;
+  key.phi = dphi;
+  key.params = dpar;
+  key.mu_eff = dmu;
+  if (!ctx->key_valid || !same_key(key, ctx->key)) {
+    drop_graph(ctx);
+    // capture one iteration on the context's stream
+    cudaStream_t c = ctx->cap;
+    KPM_CU(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+    double* ab = ctx->misc;
+    int rr = KPM_OK;
+    cudaError_t e = launch_fields(*model, dphi, dpar, 0.0, ctx->fields, nullptr, c);
+    if (e == cudaSuccess) e = launch_shift_eps(N, ctx->fields, dmu, ctx->misc + 6, ctx->misc + 2, ctx->red, c);
+    if (e == cudaSuccess) e = launch_gershgorin(*model, ctx->fields, opts->margin, ab, ctx->red, c);
+    if (e == cudaSuccess) rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c);
+    if (e == cudaSuccess && rr == KPM_OK)
+      e = launch_update(N, dpar, ctx->obs, dmu, *ropts, ctx->misc + 4, ctx->red, c);
+    if (e == cudaSuccess && rr == KPM_OK)
+      e = cudaMemcpyAsync(ctx->host_misc, ctx->misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c, &graph);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e, "capture of the RMFT iteration");
+    }
+    if (rr != KPM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rr;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->key = key;
+    ctx->key_valid = true;
+  }
+
+  kpm_rmft_stats st;
+  memset(&st, 0, sizeof(st));
+  int status = KPM_OK;
+  for (int it = 0; it < n_iter; ++it) {
+    KPM_CU(cudaGraphLaunch(ctx->graph, s));
+    KPM_CU(cudaStreamSynchronize(s));
+    const double* h = ctx->host_misc;
+    st.a = h[0];
+    st.b = h[1];
+    st.mu = h[2];
+    st.omega = h[3];
+    st.residual = h[4];
+    st.density_error = h[5];
+    st.iterations = it + 1;
+    if (!(st.residual == st.residual) || !(st.omega == st.omega) || st.residual > 1e300) {
+      status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in the RMFT iteration");
+      break;
+    }
+    st.converged = st.residual < ropts->tol && fabs(st.density_error) < ropts->tol;
+    if (st.converged) break;
+  }
+  if (!params_dev) KPM_CU(cudaMemcpyAsync(params, dpar, 26 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!mu_dev) KPM_CU(cudaMemcpyAsync(mu_eff, dmu, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!params_dev || !mu_dev) KPM_CU(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal declarations shared by the translation units of libkpm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kpm.h"
+
+namespace kpm {
+
+constexpr int kSlots = 10;     // accumulated entries per unit column (9 local rows + Omega)
+constexpr int kCoef = 26;      // complex 2h~ entries per site (both Nambu rows, padded)
+constexpr int kRedBlock = 256; // threads of the reduction kernels
+
+// Launch geometry of the recursion kernel (shared with the host planner).
+struct ChebPlan {
+  int nx, ny;
+  int64_t D;       // 2 N
+  int64_t ldv;     // slab width padded to a multiple of cb (complex elements per row)
+  int cb;          // columns per CTA
+  int ylen;        // lattice rows marched per CTA
+  int nthreads;
+  size_t smem;     // dynamic shared memory per CTA
+};
+
+// ---------------------------------------------------------------- rmft_kernels.cu
+cudaError_t launch_peierls(const kpm_model& m, double* phi, cudaStream_t s);
+// fields = dW/d(params) at chemical potential mu; wsite (N doubles) = per-site W parts
+cudaError_t launch_fields(const kpm_model& m, const double* phi, const double* params,
+                          double mu, double* fields, double* wsite, cudaStream_t s);
+// eps -= (mean(eps) + *mu_eff)   (mean over 2N site energies); mu_out = mu_eff + mean
+cudaError_t launch_shift_eps(int N, double* fields, const double* mu_eff, double* mean_scratch,
+                             double* mu_out, double* red, cudaStream_t s);
+cudaError_t launch_gershgorin(const kpm_model& m, const double* fields, double margin, double* ab,
+                              double* red, cudaStream_t s);
+// a_m (step) and a^Omega_m coefficients from device (a, b)
+cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s);
+// per-site table of 2h~ entries in precision T (kCoef complex per site)
+cudaError_t launch_scale_table_f32(const kpm_model& m, const double* fields, const double* ab,
+                                   float2* table, cudaStream_t s);
+cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, const double* ab,
+                                   double2* table, cudaStream_t s);
+// obs from accumulators; omega = a * sum Re acc[J][9] (if omega != null)
+cudaError_t launch_assemble(int N, const double2* acc, const double* ab, double* obs, double* omega,
+                            double* red, cudaStream_t s);
+// sum of a device array into *out (deterministic two-stage reduction)
+cudaError_t launch_sum(const double* x, int64_t n, double* out, double* red, cudaStream_t s);
+// RMFT mixing update; writes stats4 = {residual, density_error, -, -} and updates mu_eff
+cudaError_t launch_update(int N, double* params, double* obs, double* mu_eff, const kpm_rmft_opts& o,
+                          double* stats, double* red, cudaStream_t s);
+int reduce_scratch_doubles(int64_t n);
+
+// ---------------------------------------------------------------- cheb_kernels.cu
+ChebPlan plan_cheb(int nx, int ny, int64_t ldv_cols, int precision, int cb_request);
+cudaError_t cheb_prepare(const ChebPlan& p, int precision);
+// zero V0/acc slab, V0 = unit vectors of columns [s0, s0 + b), acc init with a_0 terms
+cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t s0,
+                             double2* acc, const double* am, const double* ao, cudaStream_t s);
+// one recursion step. mode 0: Vout = h~ Vcur (first step); mode 1: Vout = 2h~ Vcur - Vout,
+// accumulating a_m Vcur into acc (m = step index of Vcur)
+cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table, const void* Vcur,
+                             void* Vout, int64_t s0, double2* acc, const double* am,
+                             const double* ao, int m, int mode, cudaStream_t s);
+// acc += a_m V[local rows] for the slab's columns (no recursion)
+cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, int64_t s0,
+                               double2* acc, const double* am, const double* ao, int m,
+                               cudaStream_t s);
+
+}  // namespace kpm
