@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the KPM-RMFT hot path on the 100 x 100 two-vortex cell.
+
+One step = one self-consistency iteration of App. A on the 100 x 100 magnetic
+cell (10^4 sites, BdG dimension D = 20000, M = 2048 Chebyshev moments, FP32
+recursion vectors with FP64 moment sums): fields, spectral bounds,
+coefficients, the block Chebyshev recursion over all D unit start vectors,
+observable assembly and the mixing update, through the C ABI (`rmft_iterate`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own independent cell (weak
+scaling, no data-path collective); rank 0 prints one JSON line.  The
+reference arm (`--impl reference`) times the CPU oracle (naive Chebyshev
+recursion on unit vectors, FP64) on a bounded sample of the same pass.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KPM vector-moments/s & s per RMFT iteration at 100x100, FP64 vs FP32 at stated error"
+UNIT = "vector-moments/s"
+WORKLOAD = "100x100 two-vortex magnetic cell + period-8 PDW seed, D=20000, M=2048, all unit start vectors"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--block-width", type=int, default=0)
+    ap.add_argument("--cols", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-cols", type=int, default=4, help="oracle columns per worker per step")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+
+FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- oracle sample (CPU)
+
+_W = {}
+
+
+def _worker_init(nx, ny, seed, M):
+    from oracle import bdg, rmft
+    from paper_2212_05685_gb300 import inputs
+    w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), M, seed=seed, pdw=0.02)
+    model = rmft.Model(nx, ny)
+    f = rmft.fields(model, inputs.vortex_seed(w), 0.0)
+    a, b = bdg.gershgorin(model, f)
+    _W.update(h=bdg.csr(model, f), a=a, b=b, M=M)
+
+
+def _worker_run(cols):
+    from oracle import kpm
+    t0 = time.perf_counter()
+    kpm.f_naive(_W["h"], _W["a"], _W["b"], _W["M"], cols=cols)
+    return time.perf_counter() - t0
+
+
+class OracleSample:
+    """The oracle's naive KPM (scipy CSR x unit-vector block, FP64) on a column
+    sample of the benchmark pass, one spawn-started process per host core."""
+
+    def __init__(self, cols_per_worker, workers=None):
+        import multiprocessing as mp
+        from paper_2212_05685_gb300 import inputs
+        self.w = inputs.CFG2
+        self.workers = workers or len(os.sched_getaffinity(0))
+        self.cols = cols_per_worker
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.workers, initializer=_worker_init,
+                             initargs=(self.w.nx, self.w.ny, self.w.seed, self.w.M))
+        self.pool.map(_worker_run, [[0]] * self.workers)  # warm the workers
+        self.rng = 0
+
+    def step(self):
+        D = self.w.dim
+        jobs = []
+        for k in range(self.workers):
+            start = (self.rng * 7919 + k * 1013) % (D - self.cols)
+            jobs.append(list(range(start, start + self.cols)))
+        self.rng += 1
+        t0 = time.perf_counter()
+        self.pool.map(_worker_run, jobs)
+        dt = time.perf_counter() - t0
+        n = self.workers * self.cols
+        return dt, n * self.w.M / dt, n
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    samp = OracleSample(args.sample_cols)
+    for _ in range(args.warmup):
+        samp.step()
+    times, cols = [], 0
+    for _ in range(args.steps):
+        dt, _, n = samp.step()
+        times.append(dt)
+        cols += n
+    samp.close()
+    total = sum(times)
+    value = cols * samp.w.M / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 100, "ny": 100, "M": 2048, "D": 20000},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samp.workers, "kind": "oracle",
+                         "sample": f"{samp.workers * args.sample_cols} of 20000 unit columns per step "
+                                   f"(naive FP64 Chebyshev recursion, scipy CSR, M=2048)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def kernel_hash():
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_2212_05685_gb300", "csrc", "cheb_kernels.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_key, ldv):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; scaled to the benchmark's slab width."""
+    path = os.path.join(ROOT, "profiles", "cheb_step_fp32_100x100.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256_16") != kernel_key:
+        return None
+    return rec["dram_bytes_per_launch"] * ldv / rec["ldv"]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    kpm.load()
+
+    import dataclasses
+    w = dataclasses.replace(inputs.CFG2, seed=inputs.CFG2.seed + rank)
+    N, D, M = w.n_sites, w.dim, w.M
+    stream = torch.cuda.current_stream()
+    ctx = kpm.kpm_create(local)
+    model = kpm.make_model(w.nx, w.ny, w.t, w.tp, w.J, w.flux)
+    opts = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols)
+    ropts = kpm.make_rmft_opts(w.n_target, tol=0.0)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    p0 = inputs.vortex_seed(w)
+    params = torch.tensor(p0, device="cuda")
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    for _ in range(args.warmup):
+        kpm.rmft_iterate(ctx, model, opts, ropts, phi, params, mu, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rec_ms, rec_launches, launches, last = 0.0, 0, 0, None
+    for _ in range(args.steps):
+        _, st = kpm.rmft_iterate(ctx, model, opts, ropts, phi, params, mu, 1)
+        rec_ms += st.recursion_ms
+        rec_launches += st.recursion_launches
+        launches += st.kernel_launches
+        last = st
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * args.steps * D * M / t
+
+    # end to end through the public call with pinned host buffers: the step's
+    # parameters (and phases) go host->device, the updated parameters and the
+    # statistics come back, inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.tensor(p0).pin_memory()
+        hphi = phi.cpu().pin_memory()
+        hmu = torch.zeros(1, dtype=torch.float64).pin_memory()
+        kpm.rmft_iterate(ctx, model, opts, ropts, hphi, hp, hmu, 1)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            kpm.rmft_iterate(ctx, model, opts, ropts, hphi, hp, hmu, 1)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * args.steps * D * M / te, "unit": UNIT,
+               "h2d_bytes_per_step": (26 * N + 4 * N + 1) * 8,
+               "d2h_bytes_per_step": (26 * N + 1) * 8 + 8 * 8}
+
+    if rank != 0:
+        kpm.kpm_destroy(ctx)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel: the recursion step, timed live by the
+    # library's CUDA events around the step launches of every timed iteration
+    ldv = D  # D = 20000 is a multiple of every column chunk (16, 8, 4, 2)
+    per_launch_s = rec_ms / 1e3 / max(rec_launches, 1)
+    alg_bytes = 24 * D * ldv  # read V_m, read V_{m-1}, write V_{m+1}: 3 x 8 B per complex element
+    pk, pk_kind = peaks()
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = measured_traffic(kernel_hash(), ldv)
+
+    fp64 = None
+    if not args.no_fp64:
+        # FP64 recursion at M = 128, scaled to M = 2048 (cost is linear in M)
+        Ms = 128
+        fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        ab = torch.empty(2, dtype=torch.float64, device="cuda")
+        obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+        kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+        o64 = kpm.make_opts(Ms, kpm.KPM_FP64)
+        kpm.kpm_observables(ctx, model, o64, fields, ab, obs)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kpm.kpm_observables(ctx, model, o64, fields, ab, obs)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t64 = a0.elapsed_time(a1) / 1e3 * (M - 1) / (Ms - 1)
+        fp64 = {"s_per_pass": t64, "vector_moments_per_s": D * M / t64,
+                "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
+                "fp32_speedup": t64 / (t / args.steps)}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        samp = OracleSample(args.sample_cols)
+        dt, v, n = samp.step()
+        samp.close()
+        cpu = {"value": v, "unit": UNIT, "cores": samp.workers, "kind": "oracle",
+               "sample": f"{n} of {D} unit columns of one pass (naive FP64 Chebyshev recursion, scipy CSR, "
+                         f"M={M}), {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": w.nx, "ny": w.ny, "D": D, "M": M, "precision": "fp32 vectors, fp64 sums",
+                   "s_per_rmft_iteration": t / args.steps, "slab_bytes": 2 * D * ldv * 8,
+                   "l2": "inputs larger than L2 (two recursion slabs of %.1f GB)" % (D * ldv * 8 / 1e9),
+                   "parallelism": f"{world} independent cells (one per GPU)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                     "kernel": "cheb_step_kernel<float,16,1>", "peak_kind": pk_kind,
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms": per_launch_s * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fp64": fp64,
+        "residual_last": last.residual if last else None,
+    }
+    print(json.dumps(line), flush=True)
+    kpm.kpm_destroy(ctx)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def profile_small():
+    """Small case for ncu: the benchmark lattice, slabs of 2000 columns
+    (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    w = inputs.CFG2
+    N = w.n_sites
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000), fields, ab, obs)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(obs).all())
+    kpm.kpm_destroy(ctx)
+    print("profile-small done")
+    return 0
+
+
+def main():
+    args = parse()
+    if args.profile_small:
+        return profile_small()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -95,8 +95,13 @@ typedef struct {
   double mu;            /* Lagrange multiplier mu = mu_eff + <dW/dn|_{mu=0}> */
   double omega;         /* KPM grand potential Omega_M = a tr G_M(h~) of the last pass */
   double a, b;          /* spectral rescale h~ = (h - b)/a of the last pass */
+  double recursion_ms;  /* device time of the Chebyshev recursion steps, summed over
+                           this call's iterations (CUDA events recorded on the
+                           launching stream around the step launches) */
   int32_t iterations;   /* iterations performed by this call */
   int32_t converged;    /* 1 if the last iteration met tol */
+  int32_t kernel_launches;    /* kernels of this library launched per iteration */
+  int32_t recursion_launches; /* of which recursion-step launches */
 } kpm_rmft_stats;
 
 /* Create a context on CUDA device `device`.  Allocates nothing yet. */

@@ -132,22 +132,28 @@ __global__ void __launch_bounds__(256, 1)
   constexpr int VW = CT<Real>::VW;
   constexpr int NV = CB / VW;  // vectors per Nambu row of the chunk
 
+  // shared memory: V_m window [4][2 nx][CB], V_{m-1} rows [2][2 nx][CB]
+  // (step mode only), 2h~ rows [2][nx][kCoef]
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* win = reinterpret_cast<C*>(smem_raw);                  // [4][2 nx][CB]
-  C* coef = win + 4 * 2 * nx * CB;                            // [2][nx][kCoef]
   const int rowsz = 2 * nx * CB;
+  C* win = reinterpret_cast<C*>(smem_raw);
+  C* prev = win + 4 * rowsz;
+  C* coef = prev + (MODE == 1 ? 2 * rowsz : 0);
 
   const int64_t cb0 = (int64_t)blockIdx.y * CB;
   const int y0 = blockIdx.x * ylen;
   const int y1 = min(ny, y0 + ylen);
   const int nrow = y1 - y0;
 
-  // prologue: rows y0-1, y0, y0+1 and coefficients of y0; then y0+2 and y0+1
+  // prologue: V_m rows y0-1, y0, y0+1, V_{m-1} row y0, coefficients of y0;
+  // then V_m row y0+2, V_{m-1} row y0+1, coefficients of y0+1
   for (int q = 0; q < 3; ++q) stage_row<C, CB>(win + q * rowsz, Vcur, wrapi(y0 - 1 + q, ny), nx, ldv, cb0);
+  if (MODE == 1) stage_row<C, CB>(prev, Vout, y0, nx, ldv, cb0);
   stage_coef<C>(coef, table, y0, nx);
   cp_commit();
   if (nrow >= 2) {
     stage_row<C, CB>(win + 3 * rowsz, Vcur, wrapi(y0 + 2, ny), nx, ldv, cb0);
+    if (MODE == 1) stage_row<C, CB>(prev + rowsz, Vout, y0 + 1, nx, ldv, cb0);
     stage_coef<C>(coef + nx * kCoef, table, y0 + 1, nx);
   }
   cp_commit();
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(256, 1)
     const C* wm = win + (q & 3) * rowsz;        // lattice row y - 1
     const C* w0 = win + ((q + 1) & 3) * rowsz;  // y
     const C* wp = win + ((q + 2) & 3) * rowsz;  // y + 1
+    const C* pv = prev + (q & 1) * rowsz;       // V_{m-1}, row y
     const C* cf_row = coef + (q & 1) * nx * kCoef;
 
     for (int t = threadIdx.x; t < nx * NV; t += blockDim.x) {
@@ -168,16 +175,16 @@ __global__ void __launch_bounds__(256, 1)
       const int xl = x == 0 ? nx - 1 : x - 1;
       const int64_t K0 = 2 * ((int64_t)y * nx + x);
       const int64_t g0 = K0 * ldv + cb0 + v * VW;
+#define KPM_LD(W, XX, AL) (*reinterpret_cast<const V*>((W) + (2 * (XX) + (AL)) * CB + v * VW))
       V a0, a1;
       if (MODE == 1) {
-        a0 = vneg(*reinterpret_cast<const V*>(Vout + g0));
-        a1 = vneg(*reinterpret_cast<const V*>(Vout + g0 + ldv));
+        a0 = vneg(KPM_LD(pv, x, 0));
+        a1 = vneg(KPM_LD(pv, x, 1));
       } else {
         a0 = vzero<V>();
         a1 = vzero<V>();
       }
       const C* cf = cf_row + x * kCoef;
-#define KPM_LD(W, XX, AL) (*reinterpret_cast<const V*>((W) + (2 * (XX) + (AL)) * CB + v * VW))
       {
         const C d = cf[0];
         rmac(a0, d.x, KPM_LD(w0, x, 0));
@@ -228,9 +235,13 @@ __global__ void __launch_bounds__(256, 1)
       }
     }
     __syncthreads();
-    // refill: row y+3 into the buffer of y-1, coefficients of y+2
+    // refill: V_m row y+3 into the buffer of y-1, V_{m-1} row y+2 and
+    // coefficients of y+2 into the buffers of row y
     if (y + 3 <= y1) stage_row<C, CB>(win + (q & 3) * rowsz, Vcur, wrapi(y + 3, ny), nx, ldv, cb0);
-    if (y + 2 < y1) stage_coef<C>(coef + (q & 1) * nx * kCoef, table, y + 2, nx);
+    if (y + 2 < y1) {
+      if (MODE == 1) stage_row<C, CB>(prev + (q & 1) * rowsz, Vout, y + 2, nx, ldv, cb0);
+      stage_coef<C>(coef + (q & 1) * nx * kCoef, table, y + 2, nx);
+    }
     cp_commit();
   }
   cp_wait_0();
@@ -287,9 +298,9 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
 }
 
 template <typename Real, int CB>
-size_t smem_bytes(int nx) {
+size_t smem_bytes(int nx) {  // step mode (the larger of the two)
   using C = typename CT<Real>::C;
-  return sizeof(C) * ((size_t)4 * 2 * nx * CB + (size_t)2 * nx * kCoef);
+  return sizeof(C) * ((size_t)6 * 2 * nx * CB + (size_t)2 * nx * kCoef);
 }
 
 template <typename Real, int CB, int MODE>
@@ -328,6 +339,8 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   int cands64[4] = {8, 4, 2, 1};
   int* c = precision == KPM_FP32 ? cands32 : cands64;
   p.cb = 0;
+  const int min_cb = c[3];
+  if (cb_request > 0 && cb_request < min_cb) cb_request = min_cb;
   for (int k = 0; k < 4; ++k) {
     if (cb_request > 0 && c[k] > cb_request) continue;
     const size_t sm = precision == KPM_FP32

@@ -40,6 +40,11 @@ struct kpm_ctx {
   double* misc = nullptr;       // [0..1] ab, [2] mu, [3] omega, [4..5] stats, [6] mean, [7] mu_eff, [8] W
   double* host_misc = nullptr;  // pinned mirror of misc
 
+  // events around the recursion steps of the captured iteration
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int launches = 0;      // kernels per captured iteration
+  int rec_launches = 0;  // recursion-step kernels per captured iteration
+
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
   struct Key {
@@ -208,32 +213,49 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
 }
 
 // enqueue one KPM pass: fields + ab (device) -> obs, omega
+// When `events` is set, ctx->ev[0]/ev[1] are recorded on `s` around the
+// recursion-step launches (first step of the first slab to the last step of
+// the last slab); *launches / *rec_launches count the kernels enqueued.
 int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
-                 const double* ab, double* obs, double* omega, cudaStream_t s) {
+                 const double* ab, double* obs, double* omega, cudaStream_t s, bool events = false,
+                 int* launches = nullptr, int* rec_launches = nullptr) {
   const ChebPlan& p = pp.cheb;
   const int M = o->M;
   const int prec = o->precision;
+  int nl = 0, nr = 0;
   KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
   else
     KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
+  nl += 2;
   void* A = ctx->slab[0];
   void* B = ctx->slab[1];
   for (int64_t s0 = 0; s0 < p.D; s0 += pp.width) {
     KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, ctx->am, ctx->ao, s));
-    if (M >= 2) KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
+    nl += 1;
+    if (events && s0 == 0) KPM_CU(cudaEventRecord(ctx->ev[0], s));
+    if (M >= 2) {
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
+      nr += 1;
+    }
     for (int mm = 1; mm <= M - 2; ++mm) {
       const void* cur = (mm & 1) ? B : A;
       void* out = (mm & 1) ? A : B;
       KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, ctx->acc, ctx->am, ctx->ao, mm, 1, s));
+      nr += 1;
     }
+    if (events && s0 + pp.width >= p.D) KPM_CU(cudaEventRecord(ctx->ev[1], s));
     if (M >= 2) {
       const void* last = ((M - 1) & 1) ? B : A;
       KPM_CU(launch_cheb_gather(p, prec, last, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
+      nl += 1;
     }
   }
   KPM_CU(launch_assemble(m->nx * m->ny, ctx->acc, ab, obs, omega, ctx->red, s));
+  nl += omega ? 2 : 1;
+  if (launches) *launches = nl + nr;
+  if (rec_launches) *rec_launches = nr;
   return KPM_OK;
 }
 
@@ -296,8 +318,10 @@ int kpm_create(kpm_ctx** out, int device) {
   if (!ctx) return KPM_ENOMEM;
   ctx->device = device;
   DeviceGuard g(device);
-  if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess) {
     cudaGetLastError();
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
     return KPM_ECUDA;
   }
@@ -315,6 +339,8 @@ int kpm_destroy(kpm_ctx* ctx) {
                   (void*)ctx->dphi, (void*)ctx->misc})
     if (p) cudaFree(p);
   if (ctx->host_misc) cudaFreeHost(ctx->host_misc);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
   return KPM_OK;
@@ -437,7 +463,12 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     cudaError_t e = launch_fields(*model, dphi, dpar, 0.0, ctx->fields, nullptr, c);
     if (e == cudaSuccess) e = launch_shift_eps(N, ctx->fields, dmu, ctx->misc + 6, ctx->misc + 2, ctx->red, c);
     if (e == cudaSuccess) e = launch_gershgorin(*model, ctx->fields, opts->margin, ab, ctx->red, c);
-    if (e == cudaSuccess) rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c);
+    int npass = 0, nrec = 0;
+    if (e == cudaSuccess)
+      rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c, true, &npass, &nrec);
+    // fields 1, mean-shift 3, bounds 2, pass, update 4
+    ctx->launches = 1 + 3 + 2 + npass + 4;
+    ctx->rec_launches = nrec;
     if (e == cudaSuccess && rr == KPM_OK)
       e = launch_update(N, dpar, ctx->obs, dmu, *ropts, ctx->misc + 4, ctx->red, c);
     if (e == cudaSuccess && rr == KPM_OK)
@@ -466,9 +497,16 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   kpm_rmft_stats st;
   memset(&st, 0, sizeof(st));
   int status = KPM_OK;
+  st.kernel_launches = ctx->launches;
+  st.recursion_launches = ctx->rec_launches;
   for (int it = 0; it < n_iter; ++it) {
     KPM_CU(cudaGraphLaunch(ctx->graph, s));
     KPM_CU(cudaStreamSynchronize(s));
+    if (ctx->rec_launches > 0) {
+      float ms = 0.f;
+      KPM_CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+      st.recursion_ms += ms;
+    }
     const double* h = ctx->host_misc;
     st.a = h[0];
     st.b = h[1];

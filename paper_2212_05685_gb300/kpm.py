@@ -45,7 +45,8 @@ class kpm_rmft_opts(ctypes.Structure):
 class kpm_rmft_stats(ctypes.Structure):
     _fields_ = [("residual", ctypes.c_double), ("density_error", ctypes.c_double), ("mu", ctypes.c_double),
                 ("omega", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
-                ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32)]
+                ("recursion_ms", ctypes.c_double), ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("recursion_launches", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -62,4 +62,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(kpm.kpm_model) == 40
     assert ctypes.sizeof(kpm.kpm_opts) == 24
     assert ctypes.sizeof(kpm.kpm_rmft_opts) == 48
-    assert ctypes.sizeof(kpm.kpm_rmft_stats) == 56
+    assert ctypes.sizeof(kpm.kpm_rmft_stats) == 72
