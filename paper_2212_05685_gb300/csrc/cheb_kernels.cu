@@ -122,7 +122,7 @@ __device__ __forceinline__ void stage_coef(C* dst, const C* __restrict__ table, 
 }
 
 template <typename Real, int CB, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(512, 1)
     cheb_step_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const typename CT<Real>::C* __restrict__ table,
                      const typename CT<Real>::C* __restrict__ Vcur, typename CT<Real>::C* __restrict__ Vout,
                      int64_t s0, double2* __restrict__ acc, const double* __restrict__ am,
@@ -333,7 +333,7 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.nx = nx;
   p.ny = ny;
   p.D = 2 * (int64_t)nx * ny;
-  p.nthreads = 256;
+  p.nthreads = 512;
   // widest chunk that fits shared memory (FP32: 16 columns, FP64: 8)
   int cands32[4] = {16, 8, 4, 2};
   int cands64[4] = {8, 4, 2, 1};

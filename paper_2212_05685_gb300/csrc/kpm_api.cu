@@ -66,6 +66,7 @@ int fail(kpm_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(kpm_ctx* c, cudaError_t e, const char* where) {
+  cudaGetLastError();  // clear a non-sticky error so later launch checks see their own status
   return fail(c, KPM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -234,7 +235,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   for (int64_t s0 = 0; s0 < p.D; s0 += pp.width) {
     KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, ctx->am, ctx->ao, s));
     nl += 1;
-    if (events && s0 == 0) KPM_CU(cudaEventRecord(ctx->ev[0], s));
+    if (events && s0 == 0) KPM_CU(cudaEventRecordWithFlags(ctx->ev[0], s, cudaEventRecordExternal));
     if (M >= 2) {
       KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
       nr += 1;
@@ -245,7 +246,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
       KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, ctx->acc, ctx->am, ctx->ao, mm, 1, s));
       nr += 1;
     }
-    if (events && s0 + pp.width >= p.D) KPM_CU(cudaEventRecord(ctx->ev[1], s));
+    if (events && s0 + pp.width >= p.D) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
     if (M >= 2) {
       const void* last = ((M - 1) & 1) ? B : A;
       KPM_CU(launch_cheb_gather(p, prec, last, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
