@@ -157,6 +157,28 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                  const kpm_rmft_opts* ropts, const double* phi, double* params,
                  double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
 
+/* The same KPM pass as kpm_observables, for callers that cannot allocate
+ * device memory: code running under a memory manager that owns the whole
+ * device heap (a pre-sized arena that forbids other allocations) and code on
+ * a latency-critical path where cudaMalloc/cudaFree would synchronise the
+ * device.  The paper has no counterpart; this is an interface of this
+ * library only.
+ *
+ * No context and no allocation: every intermediate lives in a file-scope
+ * device array of 48 MiB (per GPU, held by every GPU that loads the library
+ * until the process exits).  The first call on a device resolves that array's
+ * address with the device current; make it before any stream capture.  All
+ * calls on a device share the array: calls whose GPU work overlaps (other
+ * streams, other host threads) race, so serialise them.  Each call rewrites
+ * every scratch byte it reads.  The recursion slab is narrowed to what fits
+ * (block_width is an upper bound); a lattice or M whose fixed intermediates
+ * (4M doubles, 26N stencil entries, 10 accumulators per column, one column
+ * chunk of both slabs) exceed 48 MiB returns KPM_EINVAL.  Arguments as for
+ * kpm_observables, with the current device; result within rounding of
+ * kpm_observables (identical arithmetic, possibly a different slab width). */
+int kpm_observables_noalloc(const kpm_model* model, const kpm_opts* opts, const double* fields,
+                            const double* ab, double* obs, double* omega, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

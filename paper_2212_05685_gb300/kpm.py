@@ -63,6 +63,8 @@ _SIGNATURES = {
     "rmft_iterate": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts),
                                     ctypes.POINTER(kpm_rmft_opts), _P, _P, _P, ctypes.c_int,
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
+    "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
+                                               _P, _P]),
 }
 
 _lib = None
@@ -197,3 +199,14 @@ def rmft_iterate(ctx: Context, model, opts, ropts, phi, params, mu_eff, n_iter, 
     if check:
         ctx.check(st, "rmft_iterate")
     return st, stats
+
+
+def kpm_observables_noalloc(model, opts, fields, ab, obs, omega=None, stream=None):
+    """kpm_observables without a context or any device allocation (for
+    callers whose device memory is owned by another allocator, or who cannot
+    afford cudaMalloc's synchronisation).  Uses the library's fixed 48 MiB
+    per-device scratch array; calls that overlap on the GPU race, so
+    serialise them.  Returns the C status (0 on success)."""
+    lib = load()
+    return lib.kpm_observables_noalloc(ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
+                                       _ptr(obs), _ptr(omega), _stream(stream))
