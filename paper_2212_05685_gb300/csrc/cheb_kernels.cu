@@ -9,16 +9,20 @@
 //
 // Layout: V is row-major, V[K][c] with K = 2 i + alpha the Nambu row and c the
 // column inside the slab; the row stride ldv is the slab width rounded up to
-// the CTA's column chunk.  h~ is a 13-point stencil per row (diagonal, eight
-// hops, four pairings), read from a per-site table of 2h~ entries.
+// the CTA's column chunk.  FP64 stores interleaved complex (re, im).  FP32
+// stores each column pair (2p, 2p+1) as (re_2p, re_2p+1, im_2p, im_2p+1) so
+// that one packed f32x2 FMA advances two columns.  h~ is a 13-point stencil
+// per row (diagonal, eight hops, four pairings), read from a per-site table
+// of 2h~ entries (FP32: each entry duplicated as (re, re, im, im)).
 //
 // Each CTA owns a chunk of CB columns and a band of lattice rows y0..y1-1.  It
 // marches along y keeping lattice rows y-1, y, y+1 of V_m (all Nx sites, both
 // Nambu components, CB columns) in shared memory, with row y+2 and the next
 // coefficient row in flight through cp.async, so every V_m element is read
 // from global memory once per CTA while serving the 13 rows that need it.
-// V_{m-1} is read and V_{m+1} written in place with coalesced 16-byte
-// accesses.  No tensor cores: the stencil is sparse, not a dense contraction.
+// V_{m-1} is read ahead (FP32: into registers one row early; FP64: through
+// cp.async) and V_{m+1} written in place with coalesced 16-byte accesses.
+// No tensor cores: the stencil is sparse, not a dense contraction.
 #include <algorithm>
 
 #include "kpm_internal.cuh"
@@ -36,52 +40,26 @@ __constant__ int kSlotFlip[kSlots] = {0, 0, 0, 0, 0, 1, 1, 1, 1, 0};
 template <typename Real>
 struct CT;
 template <>
-struct CT<float> {
-  using C = float2;  // one complex
-  using V = float4;  // VW complex values of a row
-  static constexpr int VW = 2;
-};
-template <>
 struct CT<double> {
   using C = double2;
   using V = double2;
   static constexpr int VW = 1;
 };
 
-__device__ __forceinline__ void cmac(float4& a, float2 c, float4 v) {
-  a.x = fmaf(c.x, v.x, a.x);
-  a.x = fmaf(-c.y, v.y, a.x);
-  a.y = fmaf(c.x, v.y, a.y);
-  a.y = fmaf(c.y, v.x, a.y);
-  a.z = fmaf(c.x, v.z, a.z);
-  a.z = fmaf(-c.y, v.w, a.z);
-  a.w = fmaf(c.x, v.w, a.w);
-  a.w = fmaf(c.y, v.z, a.w);
-}
 __device__ __forceinline__ void cmac(double2& a, double2 c, double2 v) {
   a.x = fma(c.x, v.x, a.x);
   a.x = fma(-c.y, v.y, a.x);
   a.y = fma(c.x, v.y, a.y);
   a.y = fma(c.y, v.x, a.y);
 }
-__device__ __forceinline__ void rmac(float4& a, float d, float4 v) {
-  a.x = fmaf(d, v.x, a.x);
-  a.y = fmaf(d, v.y, a.y);
-  a.z = fmaf(d, v.z, a.z);
-  a.w = fmaf(d, v.w, a.w);
-}
 __device__ __forceinline__ void rmac(double2& a, double d, double2 v) {
   a.x = fma(d, v.x, a.x);
   a.y = fma(d, v.y, a.y);
 }
-__device__ __forceinline__ float4 vneg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 __device__ __forceinline__ double2 vneg(double2 v) { return make_double2(-v.x, -v.y); }
-__device__ __forceinline__ float4 vscale(float4 v, float s) { return make_float4(s * v.x, s * v.y, s * v.z, s * v.w); }
 __device__ __forceinline__ double2 vscale(double2 v, double s) { return make_double2(s * v.x, s * v.y); }
 template <typename V>
 __device__ __forceinline__ V vzero();
-template <>
-__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <>
 __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 
@@ -91,6 +69,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -247,18 +226,246 @@ __global__ void __launch_bounds__(512, 1)
   cp_wait_0();
 }
 
+// ------------------------------------------------------------------ FP32 path
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 f2fma(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 f2add(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 f2sub(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 f2mul(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// value of column c in an FP32 pair-split row segment
+__device__ __forceinline__ float2 pair_elem(const float4* seg, int c) {
+  const float4 q = seg[c >> 1];
+  return (c & 1) ? make_float2(q.y, q.w) : make_float2(q.x, q.z);
+}
+
+// Accumulators of one output row for two columns: P = sum Re(c) v, Q = sum Im(c) v
+// (each a (re, im) pair of f32x2); the row value is (P.re - Q.im, P.im + Q.re).
+struct Acc2 {
+  u64 pr, pi, qr, qi;
+};
+
+__device__ __forceinline__ u64 dup2(float a) {
+  u64 d;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(a));
+  return d;
+}
+__device__ __forceinline__ void acc_term(Acc2& a, float2 c, ulonglong2 u) {
+  const u64 cr = dup2(c.x), ci = dup2(c.y);
+  a.pr = f2fma(cr, u.x, a.pr);
+  a.pi = f2fma(cr, u.y, a.pi);
+  a.qr = f2fma(ci, u.x, a.qr);
+  a.qi = f2fma(ci, u.y, a.qi);
+}
+
+// FP32 step.  Shared memory: V_m window ring of 5 lattice rows (rows y-1..y+1
+// in use, y+2 and y+3 in flight) and a ring of 3 coefficient rows (y in use,
+// y+1 and y+2 in flight); V_{m-1} rows are read one row ahead into registers.
+template <int CB, int MODE>
+__global__ void __launch_bounds__(512, 1)
+    cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
+                         const float4* __restrict__ Vcur, float4* __restrict__ Vout, int64_t s0,
+                         double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
+                         int m) {
+  constexpr int NV = CB / 2;   // float4 (column pairs) per Nambu row of the chunk
+  constexpr int RS = 2 * NV;   // float4 per site of a window row (both Nambu rows)
+  const int64_t ldq = ldv / 2; // float4 per slab row
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* win = reinterpret_cast<float4*>(smem_raw);  // [5][nx][2][NV]
+  float2* coef = reinterpret_cast<float2*>(win + 5 * nx * RS);  // [3][nx][kCoef]
+  const int rowsz = nx * RS;
+  const int crow = nx * kCoef;
+
+  const int64_t cb0 = (int64_t)blockIdx.y * CB;
+  const int64_t q0 = cb0 / 2;
+  const int y0 = blockIdx.x * ylen;
+  const int y1 = min(ny, y0 + ylen);
+  const int nrow = y1 - y0;
+
+  const int v = threadIdx.x % NV;
+  const int xs = threadIdx.x / NV;
+  const int xstep = blockDim.x / NV;  // sites of a row per thread round; nx <= 2 xstep (planner)
+  const bool own0 = xs < nx, own1 = xs + xstep < nx;
+
+  // rows of the chunk's own sites: only there are moment sums due
+  int yj_lo = ny, yj_hi = -1;
+  {
+    const int64_t Jlo = s0 + cb0, Jhi = min(D, s0 + cb0 + CB) - 1;
+    if (Jhi >= Jlo) {
+      yj_lo = (int)((Jlo >> 1) / nx);
+      yj_hi = (int)((Jhi >> 1) / nx);
+    }
+  }
+
+  // prologue groups: {V rows y0-1..y0+1, coef y0}, {V row y0+2, coef y0+1}, {V row y0+3, coef y0+2}
+  for (int q = 0; q < 3; ++q)
+    stage_row<float4, NV>(win + q * rowsz, Vcur, wrapi(y0 - 1 + q, ny), nx, ldq, q0);
+  stage_coef<float2>(coef, table, y0, nx);
+  cp_commit();
+  if (nrow >= 2) {
+    stage_row<float4, NV>(win + 3 * rowsz, Vcur, wrapi(y0 + 2, ny), nx, ldq, q0);
+    stage_coef<float2>(coef + crow, table, y0 + 1, nx);
+  }
+  cp_commit();
+  if (nrow >= 3) {
+    stage_row<float4, NV>(win + 4 * rowsz, Vcur, wrapi(y0 + 3, ny), nx, ldq, q0);
+    stage_coef<float2>(coef + 2 * crow, table, y0 + 2, nx);
+  }
+  cp_commit();
+
+  // V_{m-1} of the thread's sites, one row ahead in registers
+  ulonglong2 pc[2][2], pn[2][2];
+  const ulonglong2 zero2 = make_ulonglong2(0ull, 0ull);
+  auto load_prev = [&](int y, ulonglong2 (&dst)[2][2]) {
+    const float4* g = Vout + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
+    const int64_t gstep = 2 * (int64_t)xstep * ldq;
+    dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
+    dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
+    dst[1][0] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep) : zero2;
+    dst[1][1] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep + ldq) : zero2;
+  };
+  if (MODE == 1) load_prev(y0, pc);
+
+  const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
+  int bm = 0;  // ring slot of lattice row y - 1
+  int bc = 0;  // ring slot of the coefficients of row y
+  for (int q = 0; q < nrow; ++q) {
+    const int y = y0 + q;
+    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, pn);
+    cp_wait_2();
+    __syncthreads();
+    const int b0 = bm + 1 == 5 ? 0 : bm + 1;
+    const int bp = b0 + 1 == 5 ? 0 : b0 + 1;
+    const float4* wm = win + bm * rowsz + v;  // lattice row y - 1
+    const float4* w0 = win + b0 * rowsz + v;  // y
+    const float4* wp = win + bp * rowsz + v;  // y + 1
+    const float2* cf_row = coef + bc * crow;
+
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      if (!(it == 0 ? own0 : own1)) continue;
+      const int x = xs + it * xstep;
+      const int xr = x + 1 == nx ? 0 : x + 1;
+      const int xl = x == 0 ? nx - 1 : x - 1;
+      const float2* cf = cf_row + x * kCoef;
+#define KPM_L(W, XX, AL) (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + (AL) * NV))
+      Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
+      {
+        const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
+        const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
+        const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+        a0.pr = f2fma(d0, u0.x, a0.pr);
+        a0.pi = f2fma(d0, u0.y, a0.pi);
+        a1.pr = f2fma(d1, u1.x, a1.pr);
+        a1.pi = f2fma(d1, u1.y, a1.pi);
+      }
+      const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
+      const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
+        const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
+        acc_term(a0, cf[1 + k], u0);
+        acc_term(a1, cf[9 + k], u1);
+        if (k < 4) {
+          acc_term(a0, cf[17 + k], u1);
+          acc_term(a1, cf[21 + k], u0);
+        }
+      }
+#undef KPM_L
+      ulonglong2 o0 = make_ulonglong2(f2sub(a0.pr, a0.qi), f2add(a0.pi, a0.qr));
+      ulonglong2 o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
+      if (MODE == 1) {
+        o0.x = f2sub(o0.x, pc[it][0].x);
+        o0.y = f2sub(o0.y, pc[it][0].y);
+        o1.x = f2sub(o1.x, pc[it][1].x);
+        o1.y = f2sub(o1.y, pc[it][1].y);
+      } else {
+        o0.x = f2mul(o0.x, half2);
+        o0.y = f2mul(o0.y, half2);
+        o1.x = f2mul(o1.x, half2);
+        o1.y = f2mul(o1.y, half2);
+      }
+      float4* g = Vout + (2 * ((int64_t)y * nx + x)) * ldq + q0 + v;
+      *reinterpret_cast<ulonglong2*>(g) = o0;
+      *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
+    }
+
+    if (MODE == 1 && y >= yj_lo && y <= yj_hi) {
+      const double cm = am[m], co = ao[m];
+      for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
+        const int c = t / kSlots, s = t - c * kSlots;
+        const int64_t J = s0 + cb0 + c;
+        if (J >= D) continue;
+        const int64_t j = J >> 1;
+        if (j / nx != y) continue;
+        const int beta = (int)(J & 1);
+        const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
+        const int dy = kSlotDy[s];
+        const float4* w = (dy < 0 ? wm : (dy > 0 ? wp : w0)) - v;
+        const int al = kSlotFlip[s] ? 1 - beta : beta;
+        const float2 val = pair_elem(w + xsl * RS + al * NV, c);
+        const double coef_m = s == kSlots - 1 ? co : cm;
+        double2* a = acc + J * kSlots + s;
+        a->x += coef_m * (double)val.x;
+        a->y += coef_m * (double)val.y;
+      }
+    }
+    __syncthreads();
+    // refill: V_m row y+4 into the slot of y-1, coefficients of y+3 into the slot of y
+    if (y + 4 <= y1) stage_row<float4, NV>(win + bm * rowsz, Vcur, wrapi(y + 4, ny), nx, ldq, q0);
+    if (y + 3 < y1) stage_coef<float2>(coef + bc * crow, table, y + 3, nx);
+    cp_commit();
+    bm = b0;
+    bc = bc + 1 == 3 ? 0 : bc + 1;
+    if (MODE == 1) {
+      pc[0][0] = pn[0][0];
+      pc[0][1] = pn[0][1];
+      pc[1][0] = pn[1][0];
+      pc[1][1] = pn[1][1];
+    }
+  }
+  cp_wait_0();
+}
+
 // V0 = unit vectors e_{s0 + c} (zero elsewhere) and the m = 0 moment terms
-template <typename C>
-__global__ void cheb_init_kernel(int64_t D, int64_t ldv, C* __restrict__ V0, int64_t s0, double2* __restrict__ acc,
-                                 const double* __restrict__ am, const double* __restrict__ ao) {
+__global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, double2* __restrict__ V0, int64_t s0,
+                                     double2* __restrict__ acc, const double* __restrict__ am,
+                                     const double* __restrict__ ao) {
   const int64_t total = D * ldv;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t K = k / ldv, c = k - K * ldv;
-    C v;
-    v.x = K == s0 + c ? 1 : 0;
-    v.y = 0;
-    V0[k] = v;
+    V0[k] = make_double2(K == s0 + c ? 1.0 : 0.0, 0.0);
   }
+}
+// FP32 pair-split layout: float4 (re_2p, re_2p+1, im_2p, im_2p+1)
+__global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, float4* __restrict__ V0, int64_t s0) {
+  const int64_t ldq = ldv / 2;
+  const int64_t total = D * ldq;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t K = k / ldq, c = 2 * (k - K * ldq);
+    V0[k] = make_float4(K == s0 + c ? 1.f : 0.f, K == s0 + c + 1 ? 1.f : 0.f, 0.f, 0.f);
+  }
+}
+__global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, double2* __restrict__ acc,
+                                     const double* __restrict__ am, const double* __restrict__ ao) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ldv * kSlots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = k / kSlots;
@@ -273,8 +480,8 @@ __global__ void cheb_init_kernel(int64_t D, int64_t ldv, C* __restrict__ V0, int
 }
 
 // acc += a_m V[local rows] (the last moment, which no step reads again)
-template <typename C>
-__global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const C* __restrict__ V,
+template <bool F32>
+__global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const void* __restrict__ V,
                                    int64_t s0, double2* __restrict__ acc, const double* __restrict__ am,
                                    const double* __restrict__ ao, int m) {
   const int64_t total = width * kSlots;
@@ -289,37 +496,71 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
     const int ys = wrapi((int)(j / nx) + kSlotDy[s], ny);
     const int al = kSlotFlip[s] ? 1 - beta : beta;
     const int64_t K = 2 * ((int64_t)ys * nx + xs) + al;
-    const C val = V[K * ldv + c];
+    double re, im;
+    if (F32) {
+      const float2 val = pair_elem(reinterpret_cast<const float4*>(V) + K * (ldv / 2), (int)c);
+      re = val.x;
+      im = val.y;
+    } else {
+      const double2 val = reinterpret_cast<const double2*>(V)[K * ldv + c];
+      re = val.x;
+      im = val.y;
+    }
     const double cf = s == kSlots - 1 ? ao[m] : am[m];
     double2* a = acc + J * kSlots + s;
-    a->x += cf * (double)val.x;
-    a->y += cf * (double)val.y;
+    a->x += cf * re;
+    a->y += cf * im;
   }
 }
 
-template <typename Real, int CB>
-size_t smem_bytes(int nx) {  // step mode (the larger of the two)
-  using C = typename CT<Real>::C;
-  return sizeof(C) * ((size_t)6 * 2 * nx * CB + (size_t)2 * nx * kCoef);
+template <int CB>
+size_t smem_f32(int nx) {  // V_m window ring of 5 rows + coefficient ring of 3 rows
+  return sizeof(float4) * (size_t)5 * nx * CB + sizeof(float2) * (size_t)3 * nx * kCoef;
+}
+template <int CB>
+size_t smem_f64(int nx) {  // V_m window + V_{m-1} rows + coefficient rows
+  return sizeof(double2) * ((size_t)6 * 2 * nx * CB + (size_t)2 * nx * kCoef);
 }
 
-template <typename Real, int CB, int MODE>
-cudaError_t set_smem(int nx) {
-  return cudaFuncSetAttribute(cheb_step_kernel<Real, CB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<Real, CB>(nx));
+template <int CB>
+cudaError_t set_smem_f32(int nx) {
+  cudaError_t e = cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_f32<CB>(nx));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_f32<CB>(nx));
+}
+template <int CB>
+cudaError_t set_smem_f64(int nx) {
+  cudaError_t e = cudaFuncSetAttribute(cheb_step_kernel<double, CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_f64<CB>(nx));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_kernel<double, CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_f64<CB>(nx));
 }
 
-template <typename Real, int CB>
-cudaError_t launch_step_t(const ChebPlan& p, const void* table, const void* Vcur, void* Vout, int64_t s0,
-                          double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
-  using C = typename CT<Real>::C;
+template <int CB>
+cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, void* Vout, int64_t s0, double2* acc,
+                       const double* am, const double* ao, int m, int mode, cudaStream_t s) {
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
   if (mode == 0)
-    cheb_step_kernel<Real, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const C*)table, (const C*)Vcur, (C*)Vout, s0, acc, am, ao, m);
+    cheb_step_f32_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
+                                                                 (const float4*)Vcur, (float4*)Vout, s0, acc, am, ao, m);
   else
-    cheb_step_kernel<Real, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const C*)table, (const C*)Vcur, (C*)Vout, s0, acc, am, ao, m);
+    cheb_step_f32_kernel<CB, 1><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
+                                                                 (const float4*)Vcur, (float4*)Vout, s0, acc, am, ao, m);
+  return cudaGetLastError();
+}
+template <int CB>
+cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, void* Vout, int64_t s0, double2* acc,
+                       const double* am, const double* ao, int m, int mode, cudaStream_t s) {
+  const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
+  if (mode == 0)
+    cheb_step_kernel<double, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (double2*)Vout, s0, acc, am, ao, m);
+  else
+    cheb_step_kernel<double, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (double2*)Vout, s0, acc, am, ao, m);
   return cudaGetLastError();
 }
 
@@ -334,64 +575,61 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.ny = ny;
   p.D = 2 * (int64_t)nx * ny;
   p.nthreads = 512;
-  // widest chunk that fits shared memory (FP32: 16 columns, FP64: 8)
-  int cands32[4] = {16, 8, 4, 2};
-  int cands64[4] = {8, 4, 2, 1};
-  int* c = precision == KPM_FP32 ? cands32 : cands64;
   p.cb = 0;
-  const int min_cb = c[3];
-  if (cb_request > 0 && cb_request < min_cb) cb_request = min_cb;
+  p.ldv = 0;
+  p.smem = 0;
+  // widest column chunk that fits shared memory (FP32: 16 columns, FP64: 8);
+  // FP32 also needs every thread to own at most two sites of a lattice row
+  const int cands32[4] = {16, 8, 4, 2};
+  const int cands64[4] = {8, 4, 2, 1};
+  const int* c = precision == KPM_FP32 ? cands32 : cands64;
+  if (cb_request > 0 && cb_request < c[3]) cb_request = c[3];
   for (int k = 0; k < 4; ++k) {
     if (cb_request > 0 && c[k] > cb_request) continue;
-    const size_t sm = precision == KPM_FP32
-                          ? (c[k] == 16 ? smem_bytes<float, 16>(nx)
-                             : c[k] == 8 ? smem_bytes<float, 8>(nx)
-                             : c[k] == 4 ? smem_bytes<float, 4>(nx)
-                                         : smem_bytes<float, 2>(nx))
-                          : (c[k] == 8 ? smem_bytes<double, 8>(nx)
-                             : c[k] == 4 ? smem_bytes<double, 4>(nx)
-                             : c[k] == 2 ? smem_bytes<double, 2>(nx)
-                                         : smem_bytes<double, 1>(nx));
+    size_t sm;
+    if (precision == KPM_FP32) {
+      sm = c[k] == 16 ? smem_f32<16>(nx) : c[k] == 8 ? smem_f32<8>(nx) : c[k] == 4 ? smem_f32<4>(nx) : smem_f32<2>(nx);
+      const int xstep = p.nthreads / (c[k] / 2);
+      if (nx > 2 * xstep) continue;
+    } else {
+      sm = c[k] == 8 ? smem_f64<8>(nx) : c[k] == 4 ? smem_f64<4>(nx) : c[k] == 2 ? smem_f64<2>(nx) : smem_f64<1>(nx);
+    }
     if (sm <= kSmemLimit) {
       p.cb = c[k];
       p.smem = sm;
       break;
     }
   }
-  if (p.cb == 0) {
-    p.ldv = 0;
-    return p;
-  }
+  if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the
   // column chunks alone do not
   const int64_t chunks = p.ldv / p.cb;
   const int64_t want = 4 * kSMs;
-  int yblocks = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
+  const int yblocks = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
   p.ylen = std::max(1, (ny + yblocks - 1) / yblocks);
   return p;
 }
 
+size_t table_bytes_per_site(int precision) { return (size_t)kCoef * (precision == KPM_FP32 ? 8 : 16); }
+
 cudaError_t cheb_prepare(const ChebPlan& p, int precision) {
-  cudaError_t e = cudaSuccess;
   if (precision == KPM_FP32) {
     switch (p.cb) {
-      case 16: if ((e = set_smem<float, 16, 0>(p.nx)) == cudaSuccess) e = set_smem<float, 16, 1>(p.nx); break;
-      case 8: if ((e = set_smem<float, 8, 0>(p.nx)) == cudaSuccess) e = set_smem<float, 8, 1>(p.nx); break;
-      case 4: if ((e = set_smem<float, 4, 0>(p.nx)) == cudaSuccess) e = set_smem<float, 4, 1>(p.nx); break;
-      case 2: if ((e = set_smem<float, 2, 0>(p.nx)) == cudaSuccess) e = set_smem<float, 2, 1>(p.nx); break;
-      default: return cudaErrorInvalidValue;
+      case 16: return set_smem_f32<16>(p.nx);
+      case 8: return set_smem_f32<8>(p.nx);
+      case 4: return set_smem_f32<4>(p.nx);
+      case 2: return set_smem_f32<2>(p.nx);
     }
   } else {
     switch (p.cb) {
-      case 8: if ((e = set_smem<double, 8, 0>(p.nx)) == cudaSuccess) e = set_smem<double, 8, 1>(p.nx); break;
-      case 4: if ((e = set_smem<double, 4, 0>(p.nx)) == cudaSuccess) e = set_smem<double, 4, 1>(p.nx); break;
-      case 2: if ((e = set_smem<double, 2, 0>(p.nx)) == cudaSuccess) e = set_smem<double, 2, 1>(p.nx); break;
-      case 1: if ((e = set_smem<double, 1, 0>(p.nx)) == cudaSuccess) e = set_smem<double, 1, 1>(p.nx); break;
-      default: return cudaErrorInvalidValue;
+      case 8: return set_smem_f64<8>(p.nx);
+      case 4: return set_smem_f64<4>(p.nx);
+      case 2: return set_smem_f64<2>(p.nx);
+      case 1: return set_smem_f64<1>(p.nx);
     }
   }
-  return e;
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t s0, double2* acc, const double* am,
@@ -399,9 +637,13 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
   const int64_t total = p.D * p.ldv;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 8 * kSMs * 4);
   if (precision == KPM_FP32)
-    cheb_init_kernel<float2><<<grid, 256, 0, s>>>(p.D, p.ldv, (float2*)V0, s0, acc, am, ao);
+    cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (float4*)V0, s0);
   else
-    cheb_init_kernel<double2><<<grid, 256, 0, s>>>(p.D, p.ldv, (double2*)V0, s0, acc, am, ao);
+    cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (double2*)V0, s0, acc, am, ao);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ga = (int)std::max<int64_t>(1, std::min<int64_t>((p.ldv * kSlots + 255) / 256, 4 * kSMs));
+  cheb_init_acc_kernel<<<ga, 256, 0, s>>>(p.D, p.ldv, s0, acc, am, ao);
   return cudaGetLastError();
 }
 
@@ -410,17 +652,17 @@ cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table
                              cudaStream_t s) {
   if (precision == KPM_FP32) {
     switch (p.cb) {
-      case 16: return launch_step_t<float, 16>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 8: return launch_step_t<float, 8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 4: return launch_step_t<float, 4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 2: return launch_step_t<float, 2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 16: return launch_f32<16>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 8: return launch_f32<8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 4: return launch_f32<4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 2: return launch_f32<2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
     }
   } else {
     switch (p.cb) {
-      case 8: return launch_step_t<double, 8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 4: return launch_step_t<double, 4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 2: return launch_step_t<double, 2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 1: return launch_step_t<double, 1>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 8: return launch_f64<8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 4: return launch_f64<4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 2: return launch_f64<2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 1: return launch_f64<1>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
     }
   }
   return cudaErrorInvalidValue;
@@ -431,11 +673,9 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
   const int64_t width = p.ldv;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((width * kSlots + 255) / 256, 4 * kSMs));
   if (precision == KPM_FP32)
-    cheb_gather_kernel<float2><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, (const float2*)V, s0, acc, am,
-                                                    ao, m);
+    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, acc, am, ao, m);
   else
-    cheb_gather_kernel<double2><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, (const double2*)V, s0, acc,
-                                                     am, ao, m);
+    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, acc, am, ao, m);
   return cudaGetLastError();
 }
 

@@ -186,7 +186,7 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
   const size_t accb = (size_t)D * kSlots * sizeof(double2);
   if (ctx->acc_bytes < accb) drop_graph(ctx);
   if ((r = ensure(ctx, &ctx->acc, &ctx->acc_bytes, accb))) return r;
-  const size_t tb = (size_t)m->nx * m->ny * kCoef * pp.elem;
+  const size_t tb = (size_t)m->nx * m->ny * table_bytes_per_site(o->precision);
   if (ctx->table_bytes < tb) drop_graph(ctx);
   if ((r = ensure(ctx, &ctx->table, &ctx->table_bytes, tb))) return r;
   if (ctx->coef_n < (size_t)o->M) {

@@ -54,6 +54,8 @@ int reduce_scratch_doubles(int64_t n);
 
 // ---------------------------------------------------------------- cheb_kernels.cu
 ChebPlan plan_cheb(int nx, int ny, int64_t ldv_cols, int precision, int cb_request);
+// bytes of the per-site 2h~ table (kCoef complex entries)
+size_t table_bytes_per_site(int precision);
 cudaError_t cheb_prepare(const ChebPlan& p, int precision);
 // zero V0/acc slab, V0 = unit vectors of columns [s0, s0 + b), acc init with a_0 terms
 cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t s0,

@@ -84,7 +84,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   const size_t off_ao = align256(off_am + (size_t)o->M * sizeof(double));
   const size_t off_red = align256(off_ao + (size_t)o->M * sizeof(double));
   const size_t off_tab = align256(off_red + (size_t)reduce_scratch_doubles(0) * sizeof(double));
-  const size_t off_acc = align256(off_tab + (size_t)N * kCoef * elem);
+  const size_t off_acc = align256(off_tab + (size_t)N * table_bytes_per_site(o->precision));
   const size_t off_slab = align256(off_acc + (size_t)D * kSlots * sizeof(double2));
   if (off_slab >= kNoAllocScratchBytes) return KPM_EINVAL;  // the lattice or M exceeds the static scratch
 

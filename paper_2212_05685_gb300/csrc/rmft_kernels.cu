@@ -429,6 +429,7 @@ __device__ __forceinline__ float2 to_c<float2>(Cplx v) { return make_float2((flo
 template <>
 __device__ __forceinline__ double2 to_c<double2>(Cplx v) { return make_double2(v.re, v.im); }
 
+
 template <typename C>
 __global__ void scale_table_kernel(kpm_model m, const double* __restrict__ fld, const double* __restrict__ ab,
                                    C* __restrict__ table) {
