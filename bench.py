@@ -372,7 +372,7 @@ def run_ours(args):
                    "parallelism": f"{world} independent cells (one per GPU)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "cheb_step_kernel<float,16,1>", "peak_kind": pk_kind,
+                     "kernel": "cheb_step_f32_kernel<16,1>", "peak_kind": pk_kind,
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": per_launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
