@@ -157,6 +157,22 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                  const kpm_rmft_opts* ropts, const double* phi, double* params,
                  double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
 
+/* Reverse-mode gradient of one KPM pass (App. B, Eqs. dFdH, dalphadH): for a
+ * loss L with upstream gradients grad_obs = dL/d(obs) (26*N, the observable
+ * layout; complex entries hold (dL/dRe, dL/dIm)) and grad_omega = dL/dOmega,
+ * writes grad_fields = dL/d(eps, T, D) (26*N, field layout, same complex
+ * convention) and, when grad_phi is not NULL, grad_phi = dL/dphi (4*N)
+ * through the fields' dependence on the Peierls phases at order parameters
+ * `params` (then phi and params are required).  The rescaling ab is held
+ * fixed.  Backward recursion lambda_m = c_m + 2 h~ lambda_{m+1} -
+ * lambda_{m+2} over all D unit columns, with the forward vectors
+ * checkpointed every ckpt_every moments (0 = round(sqrt(M))) and recomputed
+ * per segment; stencil-entry sums in FP64.  Scratch: (2 ceil((M-1)/s) + s + 2)
+ * slab vectors within the context budget.  All pointers device. */
+int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
+                 const double* ab, const double* grad_obs, double grad_omega, double* grad_fields,
+                 const double* phi, const double* params, double* grad_phi, int ckpt_every, void* stream);
+
 /* The same KPM pass as kpm_observables, for callers that cannot allocate
  * device memory: code running under a memory manager that owns the whole
  * device heap (a pre-sized arena that forbids other allocations) and code on

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(512, 1)
       *reinterpret_cast<V*>(Vout + g0 + ldv) = a1;
     }
 
-    if (MODE == 1) {
+    if (MODE == 1 && acc != nullptr) {
       // moment sums of the columns whose own site lies in lattice row y
       const double cm = am[m], co = ao[m];
       for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(512, 1)
       *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
     }
 
-    if (MODE == 1 && y >= yj_lo && y <= yj_hi) {
+    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi) {
       const double cm = am[m], co = ao[m];
       for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
         const int c = t / kSlots, s = t - c * kSlots;

@@ -8,6 +8,7 @@
 #include <new>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 
 #include "kpm_internal.cuh"
@@ -38,6 +39,13 @@ struct kpm_ctx {
   double* dphi = nullptr;       // 4 N
   size_t site_n = 0;
   double* misc = nullptr;       // [0..1] ab, [2] mu, [3] omega, [4..5] stats, [6] mean, [7] mu_eff, [8] W
+  // adjoint scratch: checkpoints, segment, lambda buffers; stencil gradient; seed weights
+  void* bwd = nullptr;
+  size_t bwd_bytes = 0;
+  double2* Gacc = nullptr;
+  size_t Gacc_bytes = 0;
+  double2* wseed = nullptr;
+  size_t wseed_bytes = 0;
   double* host_misc = nullptr;  // pinned mirror of misc
 
   // events around the recursion steps of the captured iteration
@@ -160,7 +168,8 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   }
   pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
   if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
-  pp->width = width;
+  // slabs advance by the padded width: every unit column belongs to exactly one slab
+  pp->width = pp->cheb.ldv;
   return KPM_OK;
 }
 
@@ -337,7 +346,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   drop_graph(ctx);
   for (void* p : {ctx->slab[0], ctx->slab[1], (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
-                  (void*)ctx->dphi, (void*)ctx->misc})
+                  (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
     if (p) cudaFree(p);
   if (ctx->host_misc) cudaFreeHost(ctx->host_misc);
   for (cudaEvent_t e : ctx->ev)
@@ -528,6 +537,111 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   if (!params_dev || !mu_dev) KPM_CU(cudaStreamSynchronize(s));
   if (stats) *stats = st;
   return status;
+}
+
+int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
+                 const double* ab, const double* grad_obs, double grad_omega, double* grad_fields,
+                 const double* phi, const double* params, double* grad_phi, int ckpt_every, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, fields, "fields")) || (r = check_dev(ctx, ab, "ab")) ||
+      (r = check_dev(ctx, grad_obs, "grad_obs")) || (r = check_dev(ctx, grad_fields, "grad_fields")))
+    return r;
+  if (grad_phi && ((r = check_dev(ctx, grad_phi, "grad_phi")) || (r = check_dev(ctx, phi, "phi")) ||
+                   (r = check_dev(ctx, params, "params"))))
+    return r;
+  if (!opts) return fail(ctx, KPM_EINVAL, "opts is null");
+  if (ckpt_every < 0) return fail(ctx, KPM_EINVAL, "ckpt_every must be >= 0");
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  const int64_t D = 2 * (int64_t)N;
+  const int M = opts->M;
+  int seg = ckpt_every > 0 ? ckpt_every : (int)lround(sqrt((double)M));
+  if (seg < 2) seg = 2;
+  const int K = M >= 2 ? (M - 1 + seg - 1) / seg : 0;  // segments, each serving m in [k seg + 1, (k+1) seg]
+  const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
+
+  // slab width from the budget over all adjoint slab vectors (plus the forward pair)
+  kpm_opts o = *opts;
+  const size_t elem = o.precision == KPM_FP32 ? 8 : 16;
+  if (o.block_width == 0) {
+    const int64_t fit = (int64_t)(ctx->budget / ((uint64_t)(nvec + 2) * D * elem));
+    o.block_width = (int)std::max<int64_t>(1, std::min<int64_t>(D, fit));
+  }
+  PassPlan pp;
+  if ((r = plan_pass(ctx, model, &o, &pp))) return r;
+  if ((r = ensure_pass_scratch(ctx, model, &o, pp))) return r;
+  const ChebPlan& p = pp.cheb;
+  const size_t vbytes = (size_t)D * p.ldv * elem;
+  if ((r = ensure(ctx, &ctx->bwd, &ctx->bwd_bytes, vbytes * (size_t)nvec))) return r;
+  if ((r = ensure(ctx, &ctx->Gacc, &ctx->Gacc_bytes, (size_t)D * 13 * sizeof(double2)))) return r;
+  if ((r = ensure(ctx, &ctx->wseed, &ctx->wseed_bytes, (size_t)D * kSlots * sizeof(double2)))) return r;
+  char* base = static_cast<char*>(ctx->bwd);
+  auto ckpt = [&](int k) { return (void*)(base + vbytes * (size_t)k); };
+  auto segv = [&](int j) { return (void*)(base + vbytes * (size_t)(2 * K + j)); };
+  void* lamA = base + vbytes * (size_t)(2 * K + seg);
+  void* lamB = base + vbytes * (size_t)(2 * K + seg + 1);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  const int prec = o.precision;
+  void* A = ctx->slab[0];
+  void* B = ctx->slab[1];
+  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
+  if (prec == KPM_FP32)
+    KPM_CU(launch_scale_table_f32(*model, fields, ab, (float2*)ctx->table, s));
+  else
+    KPM_CU(launch_scale_table_f64(*model, fields, ab, (double2*)ctx->table, s));
+  KPM_CU(launch_seed_weights(model->nx, model->ny, grad_obs, ab, grad_omega, ctx->wseed, s));
+  KPM_CU(cudaMemsetAsync(ctx->Gacc, 0, (size_t)D * 13 * sizeof(double2), s));
+  const double* am = ctx->am;
+  const double* ao = ctx->ao;
+
+  for (int64_t s0 = 0; s0 < D && M >= 2; s0 += pp.width) {
+    // forward with checkpoints (alpha_{k seg}, alpha_{k seg + 1})
+    KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, am, ao, s));
+    KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, nullptr, am, ao, 0, 0, s));
+    KPM_CU(cudaMemcpyAsync(ckpt(0), A, vbytes, cudaMemcpyDeviceToDevice, s));
+    KPM_CU(cudaMemcpyAsync(ckpt(1), B, vbytes, cudaMemcpyDeviceToDevice, s));
+    const int last_needed = (K - 1) * seg + 1;  // highest checkpointed index
+    for (int mm = 1; mm + 1 <= last_needed; ++mm) {
+      const void* cur = (mm & 1) ? B : A;
+      void* out = (mm & 1) ? A : B;  // becomes alpha_{mm+1}
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, nullptr, am, ao, mm, 1, s));
+      const int idx = mm + 1;
+      if (idx % seg == 0 && idx / seg < K)
+        KPM_CU(cudaMemcpyAsync(ckpt(2 * (idx / seg)), out, vbytes, cudaMemcpyDeviceToDevice, s));
+      if (idx % seg == 1 && idx / seg < K)
+        KPM_CU(cudaMemcpyAsync(ckpt(2 * (idx / seg) + 1), out, vbytes, cudaMemcpyDeviceToDevice, s));
+    }
+    // backward: lambda_{m+1} in `cur`, lambda_{m+2} in `nxt`, both zero above M-1
+    void* lcur = lamA;
+    void* lnxt = lamB;
+    KPM_CU(cudaMemsetAsync(lcur, 0, vbytes, s));
+    KPM_CU(cudaMemsetAsync(lnxt, 0, vbytes, s));
+    for (int k = K - 1; k >= 0; --k) {
+      const int m_hi = std::min((k + 1) * seg, M - 1);
+      const int m_lo = k * seg + 1;
+      // recompute alpha_{k seg} .. alpha_{m_hi - 1} into the segment buffer
+      const int nseg = m_hi - 1 - k * seg + 1;
+      KPM_CU(cudaMemcpyAsync(segv(0), ckpt(2 * k), vbytes, cudaMemcpyDeviceToDevice, s));
+      if (nseg > 1) KPM_CU(cudaMemcpyAsync(segv(1), ckpt(2 * k + 1), vbytes, cudaMemcpyDeviceToDevice, s));
+      for (int j = 2; j < nseg; ++j) {
+        KPM_CU(cudaMemcpyAsync(segv(j), segv(j - 2), vbytes, cudaMemcpyDeviceToDevice, s));
+        KPM_CU(launch_cheb_step(p, prec, ctx->table, segv(j - 1), segv(j), s0, nullptr, am, ao, 0, 1, s));
+      }
+      for (int m = m_hi; m >= m_lo; --m) {
+        // lnxt <- 2 h~ lambda_{m+1} - lambda_{m+2} + c_m = lambda_m
+        KPM_CU(launch_cheb_step(p, prec, ctx->table, lcur, lnxt, s0, nullptr, am, ao, 0, 1, s));
+        KPM_CU(launch_seed_scatter(p, prec, lnxt, s0, ctx->wseed, am, ao, m, s));
+        KPM_CU(launch_grad_accum(p, prec, lnxt, segv(m - 1 - k * seg), m == 1 ? 1.0 : 2.0, ctx->Gacc, s));
+        std::swap(lcur, lnxt);
+      }
+    }
+  }
+  KPM_CU(launch_grad_fields(model->nx, model->ny, ctx->Gacc, ab, grad_fields, s));
+  if (grad_phi) KPM_CU(launch_phi_grad(*model, phi, params, grad_fields, grad_phi, s));
+  return KPM_OK;
 }
 
 }  // extern "C"

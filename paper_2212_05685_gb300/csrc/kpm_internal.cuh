@@ -70,4 +70,20 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
                                double2* acc, const double* am, const double* ao, int m,
                                cudaStream_t s);
 
+// ---------------------------------------------------------------- kpm_adjoint.cu
+// seed weights w[J][10] of every unit column from the upstream gradients
+cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const double* ab, double g_omega,
+                                double2* w, cudaStream_t s);
+// lambda[K_s(J), c] += coef_s(m) w[J][s] over the slab's columns
+cudaError_t launch_seed_scatter(const ChebPlan& p, int prec, void* lam, int64_t s0, const double2* w,
+                                const double* am, const double* ao, int m, cudaStream_t s);
+// G[I][k] += coef sum_c lam[I, c] conj(alpha[K_k(I), c]) over the 13 stencil entries of each row
+cudaError_t launch_grad_accum(const ChebPlan& p, int prec, const void* lam, const void* alpha, double coef,
+                              double2* G, cudaStream_t s);
+// dL/d(eps, T, D) from G (gradient in h~) with h~ = (h - b)/a
+cudaError_t launch_grad_fields(int nx, int ny, const double2* G, const double* ab, double* out, cudaStream_t s);
+// dL/dphi through the fields' dependence on the Peierls phases (rmft_kernels.cu)
+cudaError_t launch_phi_grad(const kpm_model& m, const double* phi, const double* params, const double* grad_fields,
+                            double* grad_phi, cudaStream_t s);
+
 }  // namespace kpm

@@ -133,7 +133,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
     KPM_NA(launch_scale_table_f32(*m, fields, ab, (float2*)table, s));
   else
     KPM_NA(launch_scale_table_f64(*m, fields, ab, (double2*)table, s));
-  for (int64_t s0 = 0; s0 < D; s0 += width) {
+  for (int64_t s0 = 0; s0 < D; s0 += p.ldv) {  // padded width: each column in one slab
     KPM_NA(launch_cheb_init(p, prec, A, s0, acc, am, ao, s));
     if (M >= 2) KPM_NA(launch_cheb_step(p, prec, table, A, B, s0, acc, am, ao, 0, 0, s));
     for (int mm = 1; mm <= M - 2; ++mm) {

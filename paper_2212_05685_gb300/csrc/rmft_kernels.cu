@@ -545,7 +545,47 @@ __global__ void update_final(const double* __restrict__ part, int n, int N, cons
   }
 }
 
+// dL/dphi of the bond i -> i + d through T_{ij s} = -g^t_ij s t_ij e^{i phi} + ...
+// and through the site energies at both ends (the g^t derivative terms hold
+// 2 Re(t_ij chi_ij s)).  One thread per site and forward bond.
+__global__ void phi_grad_kernel(kpm_model m, const double* __restrict__ phi, const double* __restrict__ p,
+                                const double* __restrict__ gf, double* __restrict__ out) {
+  const int nx = m.nx, ny = m.ny, N = nx * ny;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * N) return;
+  const int d = t / N, i = t - d * N;
+  const Layout L{N};
+  const bool gutz = m.gutzwiller != 0;
+  const double tamp = d < 2 ? m.t : m.tp;
+  const int j = shift(i, kFwdX[d], kFwdY[d], nx, ny);
+  const SiteF si = site_factors(L.n(p, 0, i), L.n(p, 1, i), gutz);
+  const SiteF sj = site_factors(L.n(p, 0, j), L.n(p, 1, j), gutz);
+  double sn, cs;
+  sincos(phi[d * N + i], &sn, &cs);
+  const Cplx dt = cx(-tamp * sn, tamp * cs);  // d/dphi of t e^{i phi}
+  double g = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    const double gg = si.gt[s] * sj.gt[s];
+    const Cplx gT = L.chi(gf, s, d, i);
+    // Re(conj(gT) dT), dT = -gg dt
+    g += -gg * (gT.re * dt.re + gT.im * dt.im);
+    const double de2 = 2.0 * cmul(dt, L.chi(p, s, d, i)).re;
+    for (int sp = 0; sp < 2; ++sp) {
+      g += L.n(gf, sp, i) * (-si.dgt[s][sp] * sj.gt[s] * de2);
+      g += L.n(gf, sp, j) * (-sj.dgt[s][sp] * si.gt[s] * de2);
+    }
+  }
+  out[d * N + i] = g;
+}
+
 }  // namespace
+
+cudaError_t launch_phi_grad(const kpm_model& m, const double* phi, const double* params, const double* grad_fields,
+                            double* grad_phi, cudaStream_t s) {
+  const int N = m.nx * m.ny;
+  phi_grad_kernel<<<(4 * N + 127) / 128, 128, 0, s>>>(m, phi, params, grad_fields, grad_phi);
+  return cudaGetLastError();
+}
 
 int reduce_scratch_doubles(int64_t) { return 2 * kRedGrid + 16; }
 

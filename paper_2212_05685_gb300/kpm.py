@@ -65,6 +65,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
     "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
                                                _P, _P]),
+    "kpm_backward": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
+                                    ctypes.c_double, _P, _P, _P, _P, ctypes.c_int, _P]),
 }
 
 _lib = None
@@ -199,6 +201,14 @@ def rmft_iterate(ctx: Context, model, opts, ropts, phi, params, mu_eff, n_iter, 
     if check:
         ctx.check(st, "rmft_iterate")
     return st, stats
+
+
+def kpm_backward(ctx: Context, model, opts, fields, ab, grad_obs, grad_omega, grad_fields, phi=None, params=None,
+                 grad_phi=None, ckpt_every=0, stream=None):
+    return ctx.check(ctx.lib.kpm_backward(ctx.handle, ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
+                                          _ptr(grad_obs), float(grad_omega), _ptr(grad_fields), _ptr(phi),
+                                          _ptr(params), _ptr(grad_phi), int(ckpt_every), _stream(stream)),
+                     "kpm_backward")
 
 
 def kpm_observables_noalloc(model, opts, fields, ab, obs, omega=None, stream=None):
