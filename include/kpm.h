@@ -157,6 +157,21 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                  const kpm_rmft_opts* ropts, const double* phi, double* params,
                  double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
 
+/* Batched self-consistency (cells of uneven size, doping and field): up to
+ * n_iter iterations of rmft_iterate's loop for ncell independent cells,
+ * replayed as one CUDA graph per iteration.  Cells of equal (nx, ny) share
+ * one batched recursion launch per Chebyshev step (FP32; FP64 runs the cells
+ * of a shape in sequence), and the shape classes run on concurrent streams.
+ * models, ropts, phis, params, stats: arrays of ncell entries (host arrays;
+ * phis[c] and params[c] device pointers of 4N_c and 26N_c doubles, updated in
+ * place); mu_eff: device array of ncell doubles (updated); opts shared (M,
+ * precision).  At most 64 cells of one shape in FP32.  Stops early when every
+ * cell meets its tol; stats[c] as in rmft_iterate (recursion timing not
+ * recorded). */
+int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const kpm_opts* opts,
+                         const kpm_rmft_opts* ropts, const double* const* phis, double* const* params,
+                         double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
+
 /* Reverse-mode gradient of one KPM pass (App. B, Eqs. dFdH, dalphadH): for a
  * loss L with upstream gradients grad_obs = dL/d(obs) (26*N, the observable
  * layout; complex entries hold (dL/dRe, dL/dIm)) and grad_omega = dL/dOmega,

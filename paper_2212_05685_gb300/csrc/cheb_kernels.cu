@@ -278,11 +278,10 @@ __device__ __forceinline__ void acc_term(Acc2& a, float2 c, ulonglong2 u) {
 // in use, y+2 and y+3 in flight) and a ring of 3 coefficient rows (y in use,
 // y+1 and y+2 in flight); V_{m-1} rows are read one row ahead into registers.
 template <int CB, int MODE>
-__global__ void __launch_bounds__(512, 1)
-    cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
-                         const float4* __restrict__ Vcur, float4* __restrict__ Vout, int64_t s0,
-                         double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
-                         int m) {
+__device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
+                                              const float2* __restrict__ table, const float4* __restrict__ Vcur,
+                                              float4* __restrict__ Vout, int64_t s0, double2* __restrict__ acc,
+                                              const double* __restrict__ am, const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;   // float4 (column pairs) per Nambu row of the chunk
   constexpr int RS = 2 * NV;   // float4 per site of a window row (both Nambu rows)
   const int64_t ldq = ldv / 2; // float4 per slab row
@@ -445,6 +444,31 @@ __global__ void __launch_bounds__(512, 1)
   cp_wait_0();
 }
 
+template <int CB, int MODE>
+__global__ void __launch_bounds__(512, 1)
+    cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
+                         const float4* __restrict__ Vcur, float4* __restrict__ Vout, int64_t s0,
+                         double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
+                         int m) {
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vout, s0, acc, am, ao, m);
+}
+
+// Batched step: cells of one shape, blockIdx.z selects the cell; every cell
+// is one full-width slab (s0 = 0).
+template <int CB, int MODE>
+__global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, int ny, int64_t D, int64_t ldv,
+                                                                        int ylen, BatchPtrs b, int m) {
+  const int z = blockIdx.z;
+  const float4* cur = reinterpret_cast<const float4*>((m & 1) ? b.B[z] : b.A[z]);
+  float4* out = reinterpret_cast<float4*>((m & 1) ? b.A[z] : b.B[z]);
+  if (MODE == 0) {
+    cur = reinterpret_cast<const float4*>(b.A[z]);
+    out = reinterpret_cast<float4*>(b.B[z]);
+  }
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, 0, b.acc[z],
+                          b.am[z], b.ao[z], m);
+}
+
 // V0 = unit vectors e_{s0 + c} (zero elsewhere) and the m = 0 moment terms
 __global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, double2* __restrict__ V0, int64_t s0,
                                      double2* __restrict__ acc, const double* __restrict__ am,
@@ -513,6 +537,9 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
   }
 }
 
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kSMs = 152;
+
 template <int CB>
 size_t smem_f32(int nx) {  // V_m window ring of 5 rows + coefficient ring of 3 rows
   return sizeof(float4) * (size_t)5 * nx * CB + sizeof(float2) * (size_t)3 * nx * kCoef;
@@ -525,18 +552,36 @@ size_t smem_f64(int nx) {  // V_m window + V_{m-1} rows + coefficient rows
 template <int CB>
 cudaError_t set_smem_f32(int nx) {
   cudaError_t e = cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_f32<CB>(nx));
+                                       (int)kSmemLimit);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_f32<CB>(nx));
+                              (int)kSmemLimit);
 }
+template <int CB>
+cudaError_t set_smem_f32_batched(int nx) {
+  cudaError_t e = cudaFuncSetAttribute(cheb_step_f32_batched_kernel<CB, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_f32_batched_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSmemLimit);
+}
+template <int CB>
+cudaError_t launch_f32_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode, cudaStream_t s) {
+  const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB), (unsigned)ncell);
+  if (mode == 0)
+    cheb_step_f32_batched_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, b, m);
+  else
+    cheb_step_f32_batched_kernel<CB, 1><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, b, m);
+  return cudaGetLastError();
+}
+
 template <int CB>
 cudaError_t set_smem_f64(int nx) {
   cudaError_t e = cudaFuncSetAttribute(cheb_step_kernel<double, CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_f64<CB>(nx));
+                                       (int)kSmemLimit);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(cheb_step_kernel<double, CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_f64<CB>(nx));
+                              (int)kSmemLimit);
 }
 
 template <int CB>
@@ -564,8 +609,6 @@ cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, v
   return cudaGetLastError();
 }
 
-constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kSMs = 152;
 
 }  // namespace
 
@@ -664,6 +707,27 @@ cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table
       case 2: return launch_f64<2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
       case 1: return launch_f64<1>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
     }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t cheb_prepare_batched(const ChebPlan& p) {
+  switch (p.cb) {
+    case 16: return set_smem_f32_batched<16>(p.nx);
+    case 8: return set_smem_f32_batched<8>(p.nx);
+    case 4: return set_smem_f32_batched<4>(p.nx);
+    case 2: return set_smem_f32_batched<2>(p.nx);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
+                                     cudaStream_t s) {
+  switch (p.cb) {
+    case 16: return launch_f32_batched<16>(p, ncell, b, m, mode, s);
+    case 8: return launch_f32_batched<8>(p, ncell, b, m, mode, s);
+    case 4: return launch_f32_batched<4>(p, ncell, b, m, mode, s);
+    case 2: return launch_f32_batched<2>(p, ncell, b, m, mode, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -9,7 +9,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <string>
+#include <vector>
 
 #include "kpm_internal.cuh"
 
@@ -52,6 +54,25 @@ struct kpm_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int launches = 0;      // kernels per captured iteration
   int rec_launches = 0;  // recursion-step kernels per captured iteration
+
+  // batched iteration: per-cell scratch, fork streams, cached graph
+  struct Cell {
+    void* mem = nullptr;  // one allocation per cell
+    size_t bytes = 0;
+    double *fields, *obs, *am, *ao, *misc;
+    double2* acc;
+    void *table, *A, *B;
+    int cls;
+  };
+  std::vector<Cell> cells;
+  std::vector<cudaStream_t> fork;
+  std::vector<cudaEvent_t> fork_ev;
+  cudaEvent_t join_ev = nullptr;
+  double* bred = nullptr;          // reduction partials (cells run in sequence on one stream)
+  double* bhost = nullptr;         // pinned mirror of the cells' misc blocks
+  size_t bhost_n = 0;
+  cudaGraphExec_t bgraph = nullptr;
+  std::vector<char> bkey;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -349,6 +370,14 @@ int kpm_destroy(kpm_ctx* ctx) {
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
     if (p) cudaFree(p);
   if (ctx->host_misc) cudaFreeHost(ctx->host_misc);
+  if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+  for (auto& c : ctx->cells)
+    if (c.mem) cudaFree(c.mem);
+  for (cudaStream_t st : ctx->fork) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->fork_ev) cudaEventDestroy(e);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+  if (ctx->bred) cudaFree(ctx->bred);
+  if (ctx->bhost) cudaFreeHost(ctx->bhost);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -642,6 +671,261 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   KPM_CU(launch_grad_fields(model->nx, model->ny, ctx->Gacc, ab, grad_fields, s));
   if (grad_phi) KPM_CU(launch_phi_grad(*model, phi, params, grad_fields, grad_phi, s));
   return KPM_OK;
+}
+
+int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const kpm_opts* opts,
+                         const kpm_rmft_opts* ropts, const double* const* phis, double* const* params,
+                         double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  if (ncell < 1 || ncell > 4096 || !models || !opts || !ropts || !phis || !params || !mu_eff || n_iter < 0)
+    return fail(ctx, KPM_EINVAL, "bad batch arguments");
+  int r;
+  for (int c = 0; c < ncell; ++c) {
+    if ((r = check_model(ctx, &models[c]))) return r;
+    if ((r = check_dev(ctx, phis[c], "phis[c]")) || (r = check_dev(ctx, params[c], "params[c]"))) return r;
+    if (!(ropts[c].alpha > 0.0 && ropts[c].alpha <= 1.0 && ropts[c].alpha_n > 0.0 && ropts[c].alpha_n <= 1.0))
+      return fail(ctx, KPM_EINVAL, "mixing must lie in (0, 1]");
+  }
+  if ((r = check_dev(ctx, mu_eff, "mu_eff"))) return r;
+  if (opts->M < 1 || (opts->precision != KPM_FP32 && opts->precision != KPM_FP64))
+    return fail(ctx, KPM_EINVAL, "bad opts");
+  DeviceGuard g(ctx->device);
+  const int M = opts->M, prec = opts->precision;
+  const size_t elem = prec == KPM_FP32 ? 8 : 16;
+
+  // shape classes (cells of equal nx, ny share one batched launch per step)
+  std::map<std::pair<int, int>, int> cls_of;
+  std::vector<std::vector<int>> members;
+  for (int c = 0; c < ncell; ++c) {
+    auto key = std::make_pair(models[c].nx, models[c].ny);
+    auto it = cls_of.find(key);
+    if (it == cls_of.end()) {
+      it = cls_of.emplace(key, (int)members.size()).first;
+      members.emplace_back();
+    }
+    members[it->second].push_back(c);
+  }
+  for (auto& v : members)
+    if ((int)v.size() > kMaxBatch && prec == KPM_FP32) return fail(ctx, KPM_EINVAL, "more than 64 cells of one shape");
+  std::vector<ChebPlan> plans(members.size());
+  for (size_t k = 0; k < members.size(); ++k) {
+    const kpm_model& m0 = models[members[k][0]];
+    const int64_t D = 2 * (int64_t)m0.nx * m0.ny;
+    plans[k] = plan_cheb(m0.nx, m0.ny, D, prec, opts->cols_per_block);
+    if (plans[k].cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
+    // spread one step over the whole batch: y bands so that every cell fills its share
+    const int64_t chunks = plans[k].ldv / plans[k].cb;
+    const int64_t want = std::max<int64_t>(1, 4 * 152 / (int64_t)std::max<size_t>(1, members[k].size()));
+    const int yb = (int)std::min<int64_t>(m0.ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
+    plans[k].ylen = std::max(1, (m0.ny + yb - 1) / yb);
+    cudaError_t e = prec == KPM_FP32 ? cheb_prepare_batched(plans[k]) : cheb_prepare(plans[k], prec);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "prepare");
+  }
+
+  // per-cell scratch, one allocation per cell
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  bool realloc = (int)ctx->cells.size() != ncell;
+  std::vector<size_t> need(ncell);
+  for (int c = 0; c < ncell; ++c) {
+    const int N = models[c].nx * models[c].ny;
+    const int64_t D = 2 * (int64_t)N;
+    const int k = cls_of[std::make_pair(models[c].nx, models[c].ny)];
+    need[c] = al(26 * (size_t)N * 8) * 2 + al((size_t)M * 8) * 2 + al(16 * 8) + al((size_t)D * kSlots * 16) +
+              al((size_t)N * table_bytes_per_site(prec)) + 2 * al((size_t)D * plans[k].ldv * elem);
+    if (!realloc && ctx->cells[c].bytes < need[c]) realloc = true;
+  }
+  if (realloc) {
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    ctx->bkey.clear();
+    for (auto& c : ctx->cells)
+      if (c.mem) cudaFree(c.mem);
+    ctx->cells.assign(ncell, kpm_ctx::Cell());
+    for (int c = 0; c < ncell; ++c) {
+      if (cudaMalloc(&ctx->cells[c].mem, need[c]) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cells[c].mem = nullptr;
+        return fail(ctx, KPM_ENOMEM, "cudaMalloc of batch scratch failed");
+      }
+      ctx->cells[c].bytes = need[c];
+    }
+  }
+  for (int c = 0; c < ncell; ++c) {
+    const int N = models[c].nx * models[c].ny;
+    const int64_t D = 2 * (int64_t)N;
+    const int k = cls_of[std::make_pair(models[c].nx, models[c].ny)];
+    char* b = static_cast<char*>(ctx->cells[c].mem);
+    kpm_ctx::Cell& C = ctx->cells[c];
+    C.fields = (double*)b; b += al(26 * (size_t)N * 8);
+    C.obs = (double*)b; b += al(26 * (size_t)N * 8);
+    C.am = (double*)b; b += al((size_t)M * 8);
+    C.ao = (double*)b; b += al((size_t)M * 8);
+    C.misc = (double*)b; b += al(16 * 8);
+    C.acc = (double2*)b; b += al((size_t)D * kSlots * 16);
+    C.table = b; b += al((size_t)N * table_bytes_per_site(prec));
+    C.A = b; b += al((size_t)D * plans[k].ldv * elem);
+    C.B = b;
+    C.cls = k;
+  }
+  if (!ctx->bred && cudaMalloc(&ctx->bred, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  if (ctx->bhost_n < (size_t)ncell * 16) {
+    if (ctx->bhost) cudaFreeHost(ctx->bhost);
+    ctx->bhost = nullptr;
+    if (cudaMallocHost(&ctx->bhost, (size_t)ncell * 16 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, KPM_ENOMEM, "cudaMallocHost failed");
+    }
+    ctx->bhost_n = (size_t)ncell * 16;
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    ctx->bkey.clear();
+  }
+  while (ctx->fork.size() < members.size()) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, KPM_ECUDA, "stream creation failed");
+    }
+    ctx->fork.push_back(st);
+    ctx->fork_ev.push_back(ev);
+  }
+  if (!ctx->join_ev && cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ECUDA, "event creation failed");
+  }
+
+  // graph key: everything the captured work depends on
+  std::vector<char> key;
+  auto put = [&](const void* p, size_t n) { key.insert(key.end(), (const char*)p, (const char*)p + n); };
+  put(&ncell, sizeof(ncell));
+  put(models, sizeof(kpm_model) * ncell);
+  put(opts, sizeof(kpm_opts));
+  put(ropts, sizeof(kpm_rmft_opts) * ncell);
+  put(phis, sizeof(double*) * ncell);
+  put(params, sizeof(double*) * ncell);
+  put(&mu_eff, sizeof(mu_eff));
+  if (!ctx->bgraph || key != ctx->bkey) {
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    cudaStream_t c0 = ctx->cap;
+    KPM_CU(cudaStreamBeginCapture(c0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const char* where = "";
+#define KPM_TRY(expr)        \
+  do {                       \
+    if (e == cudaSuccess) {  \
+      e = (expr);            \
+      if (e != cudaSuccess) where = #expr; \
+    }                        \
+  } while (0)
+    for (int c = 0; c < ncell; ++c) {
+      kpm_ctx::Cell& C = ctx->cells[c];
+      const kpm_model& m = models[c];
+      const int N = m.nx * m.ny;
+      const ChebPlan& p = plans[C.cls];
+      KPM_TRY(launch_fields(m, phis[c], params[c], 0.0, C.fields, nullptr, c0));
+      KPM_TRY(launch_shift_eps(N, C.fields, mu_eff + c, C.misc + 6, C.misc + 2, ctx->bred, c0));
+      KPM_TRY(launch_gershgorin(m, C.fields, opts->margin, C.misc, ctx->bred, c0));
+      KPM_TRY(launch_coefficients(M, C.misc, C.am, C.ao, c0));
+      if (prec == KPM_FP32)
+        KPM_TRY(launch_scale_table_f32(m, C.fields, C.misc, (float2*)C.table, c0));
+      else
+        KPM_TRY(launch_scale_table_f64(m, C.fields, C.misc, (double2*)C.table, c0));
+      KPM_TRY(launch_cheb_init(p, prec, C.A, 0, C.acc, C.am, C.ao, c0));
+    }
+    // recursion: one chain per shape class on its own stream
+    KPM_TRY(cudaEventRecord(ctx->join_ev, c0));
+    for (size_t k = 0; k < members.size() && M >= 2; ++k) {
+      cudaStream_t sk = ctx->fork[k];
+      KPM_TRY(cudaStreamWaitEvent(sk, ctx->join_ev, 0));
+      const ChebPlan& p = plans[k];
+      if (prec == KPM_FP32) {
+        BatchPtrs bp;
+        memset(&bp, 0, sizeof(bp));
+        for (size_t z = 0; z < members[k].size(); ++z) {
+          kpm_ctx::Cell& C = ctx->cells[members[k][z]];
+          bp.A[z] = C.A;
+          bp.B[z] = C.B;
+          bp.table[z] = C.table;
+          bp.acc[z] = C.acc;
+          bp.am[z] = C.am;
+          bp.ao[z] = C.ao;
+        }
+        const int nz = (int)members[k].size();
+        KPM_TRY(launch_cheb_step_batched(p, nz, bp, 0, 0, sk));
+        for (int mm = 1; mm <= M - 2; ++mm) KPM_TRY(launch_cheb_step_batched(p, nz, bp, mm, 1, sk));
+      } else {
+        for (size_t z = 0; z < members[k].size(); ++z) {
+          kpm_ctx::Cell& C = ctx->cells[members[k][z]];
+          KPM_TRY(launch_cheb_step(p, prec, C.table, C.A, C.B, 0, C.acc, C.am, C.ao, 0, 0, sk));
+          for (int mm = 1; mm <= M - 2; ++mm) {
+            const void* cur = (mm & 1) ? C.B : C.A;
+            void* out = (mm & 1) ? C.A : C.B;
+            KPM_TRY(launch_cheb_step(p, prec, C.table, cur, out, 0, C.acc, C.am, C.ao, mm, 1, sk));
+          }
+        }
+      }
+      KPM_TRY(cudaEventRecord(ctx->fork_ev[k], sk));
+      KPM_TRY(cudaStreamWaitEvent(c0, ctx->fork_ev[k], 0));
+    }
+    for (int c = 0; c < ncell; ++c) {
+      kpm_ctx::Cell& C = ctx->cells[c];
+      const int N = models[c].nx * models[c].ny;
+      const ChebPlan& p = plans[C.cls];
+      if (M >= 2) KPM_TRY(launch_cheb_gather(p, prec, ((M - 1) & 1) ? C.B : C.A, 0, C.acc, C.am, C.ao, M - 1, c0));
+      KPM_TRY(launch_assemble(N, C.acc, C.misc, C.obs, C.misc + 3, ctx->bred, c0));
+      KPM_TRY(launch_update(N, params[c], C.obs, mu_eff + c, ropts[c], C.misc + 4, ctx->bred, c0));
+      KPM_TRY(cudaMemcpyAsync(ctx->bhost + 16 * c, C.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c0));
+    }
+#undef KPM_TRY
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c0, &graph);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e, (std::string("capture of the batched iteration at ") + where).c_str());
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->bgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->bgraph = nullptr;
+      return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->bkey = key;
+  }
+
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<kpm_rmft_stats> st(ncell);
+  memset(st.data(), 0, sizeof(kpm_rmft_stats) * ncell);
+  int status = KPM_OK;
+  for (int it = 0; it < n_iter; ++it) {
+    KPM_CU(cudaGraphLaunch(ctx->bgraph, s));
+    KPM_CU(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int c = 0; c < ncell; ++c) {
+      const double* h = ctx->bhost + 16 * c;
+      kpm_rmft_stats& q = st[c];
+      q.a = h[0];
+      q.b = h[1];
+      q.mu = h[2];
+      q.omega = h[3];
+      q.residual = h[4];
+      q.density_error = h[5];
+      q.iterations = it + 1;
+      if (!(q.residual == q.residual) || !(q.omega == q.omega) || q.residual > 1e300)
+        status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in a batched cell");
+      q.converged = q.residual < ropts[c].tol && fabs(q.density_error) < ropts[c].tol;
+      all = all && q.converged;
+    }
+    if (status != KPM_OK || all) break;
+  }
+  if (stats) memcpy(stats, st.data(), sizeof(kpm_rmft_stats) * ncell);
+  return status;
 }
 
 }  // extern "C"

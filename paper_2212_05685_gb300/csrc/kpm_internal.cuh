@@ -25,6 +25,17 @@ struct ChebPlan {
   size_t smem;     // dynamic shared memory per CTA
 };
 
+// Per-cell pointers of a batch of equally shaped cells (FP32 recursion).
+constexpr int kMaxBatch = 64;
+struct BatchPtrs {
+  void* A[kMaxBatch];
+  void* B[kMaxBatch];
+  const void* table[kMaxBatch];
+  double2* acc[kMaxBatch];
+  const double* am[kMaxBatch];
+  const double* ao[kMaxBatch];
+};
+
 // ---------------------------------------------------------------- rmft_kernels.cu
 cudaError_t launch_peierls(const kpm_model& m, double* phi, cudaStream_t s);
 // fields = dW/d(params) at chemical potential mu; wsite (N doubles) = per-site W parts
@@ -65,6 +76,10 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
 cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table, const void* Vcur,
                              void* Vout, int64_t s0, double2* acc, const double* am,
                              const double* ao, int m, int mode, cudaStream_t s);
+// batched FP32 step over ncell cells of one shape (plan p, full-width slabs)
+cudaError_t cheb_prepare_batched(const ChebPlan& p);
+cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
+                                     cudaStream_t s);
 // acc += a_m V[local rows] for the slab's columns (no recursion)
 cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, int64_t s0,
                                double2* acc, const double* am, const double* ao, int m,

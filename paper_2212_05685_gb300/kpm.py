@@ -65,6 +65,10 @@ _SIGNATURES = {
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
     "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
                                                _P, _P]),
+    "rmft_iterate_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts),
+                                            ctypes.POINTER(kpm_rmft_opts), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_int,
+                                            ctypes.POINTER(kpm_rmft_stats), _P]),
     "kpm_backward": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
                                     ctypes.c_double, _P, _P, _P, _P, ctypes.c_int, _P]),
 }
@@ -201,6 +205,23 @@ def rmft_iterate(ctx: Context, model, opts, ropts, phi, params, mu_eff, n_iter, 
     if check:
         ctx.check(st, "rmft_iterate")
     return st, stats
+
+
+def rmft_iterate_batched(ctx: Context, models, opts, ropts, phis, params, mu_eff, n_iter, stream=None, check=True):
+    """Batched iterations of independent cells; models/ropts: lists of structs,
+    phis/params: lists of CUDA tensors, mu_eff: CUDA tensor of len(models).
+    Returns (status, list of kpm_rmft_stats)."""
+    n = len(models)
+    M_arr = (kpm_model * n)(*models)
+    R_arr = (kpm_rmft_opts * n)(*ropts)
+    P_arr = (ctypes.c_void_p * n)(*[x.data_ptr() for x in phis])
+    Q_arr = (ctypes.c_void_p * n)(*[x.data_ptr() for x in params])
+    S_arr = (kpm_rmft_stats * n)()
+    st = ctx.lib.rmft_iterate_batched(ctx.handle, n, M_arr, ctypes.byref(opts), R_arr, P_arr, Q_arr, _ptr(mu_eff),
+                                      int(n_iter), S_arr, _stream(stream))
+    if check:
+        ctx.check(st, "rmft_iterate_batched")
+    return st, list(S_arr)
 
 
 def kpm_backward(ctx: Context, model, opts, fields, ab, grad_obs, grad_omega, grad_fields, phi=None, params=None,
