@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-cols", type=int, default=4, help="oracle columns per worker per step")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
     return ap.parse_args()
@@ -259,6 +262,20 @@ def run_ours(args):
     params = torch.tensor(p0, device="cuda")
     mu = torch.zeros(1, dtype=torch.float64, device="cuda")
 
+    # recursion launch configuration: the library's autotuner (slab width,
+    # column chunk) on this cell's Hamiltonian, unless fixed on the command line
+    tune = None
+    if not args.no_autotune and args.block_width == 0 and args.cols == 0:
+        f0 = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        ab0 = torch.empty(2, dtype=torch.float64, device="cuda")
+        kpm.kpm_build_H(ctx, model, phi, params, 0.0, f0)
+        kpm.kpm_bounds(ctx, model, f0, 0.01, ab0)
+        t0 = time.perf_counter()
+        opts, ms_step = kpm.kpm_autotune(ctx, model, opts, f0, ab0)
+        tune = {"block_width": opts.block_width, "cols_per_block": opts.cols_per_block,
+                "trial_ms_per_step": ms_step, "tuning_s": time.perf_counter() - t0}
+        del f0, ab0
+
     for _ in range(args.warmup):
         kpm.rmft_iterate(ctx, model, opts, ropts, phi, params, mu, 1)
     torch.cuda.synchronize()
@@ -322,12 +339,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel: the recursion step, timed live by the
     # library's CUDA events around the step launches of every timed iteration
-    ldv = D  # D = 20000 is a multiple of every column chunk (16, 8, 4, 2)
+    cb = opts.cols_per_block if opts.cols_per_block > 0 else 16
+    width = opts.block_width if 0 < opts.block_width < D else D
+    ldv = (width + cb - 1) // cb * cb
     per_launch_s = rec_ms / 1e3 / max(rec_launches, 1)
     alg_bytes = 24 * D * ldv  # read V_m, read V_{m-1}, write V_{m+1}: 3 x 8 B per complex element
     pk, pk_kind = peaks()
     achieved = alg_bytes / per_launch_s / 1e9
-    traffic = measured_traffic(kernel_hash(), ldv)
+    # the committed ncu counters were taken on a slab larger than L2; they
+    # scale to full-width slabs only
+    traffic = measured_traffic(kernel_hash(), ldv) if width == D else None
 
     fp64 = None
     if not args.no_fp64:
@@ -352,6 +373,9 @@ def run_ours(args):
                 "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
                 "fp32_speedup": t64 / (t / args.steps)}
 
+    batched = None if args.no_batched else batched_section(kpm, inputs, torch)
+    adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         samp = OracleSample(args.sample_cols)
@@ -367,8 +391,10 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": w.nx, "ny": w.ny, "D": D, "M": M, "precision": "fp32 vectors, fp64 sums",
+                   "slab_width": width, "cols_per_block": cb, "autotune": tune,
                    "s_per_rmft_iteration": t / args.steps, "slab_bytes": 2 * D * ldv * 8,
-                   "l2": "inputs larger than L2 (two recursion slabs of %.1f GB)" % (D * ldv * 8 / 1e9),
+                   "l2": ("inputs larger than L2 (two recursion slabs of %.2f GB)" % (D * ldv * 8 / 1e9))
+                   if 2 * D * ldv * 8 > 129e6 else "recursion slabs L2-resident (%.0f MB)" % (2 * D * ldv * 8 / 1e6),
                    "parallelism": f"{world} independent cells (one per GPU)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
@@ -379,6 +405,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "fp64": fp64,
+        "batched": batched,
+        "adjoint": adjoint,
         "residual_last": last.residual if last else None,
     }
     print(json.dumps(line), flush=True)
@@ -387,6 +415,83 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def batched_section(kpm, inputs, torch, iters=3):
+    """32 cells of uneven size and doping (shapes 24x12 .. 64x32), M = 1024,
+    FP32: one batched graph per iteration vs the cells one after another."""
+    cells = inputs.cfg3_cells(seed=0, count=32)
+    M = 1024
+    opts = kpm.make_opts(M, kpm.KPM_FP32)
+    ctx = kpm.kpm_create(0)
+    models, phis, params, ropts = [], [], [], []
+    for w in cells:
+        m = kpm.make_model(w.nx, w.ny)
+        phi = torch.empty(4 * w.n_sites, dtype=torch.float64, device="cuda")
+        kpm.kpm_peierls_phases(ctx, m, phi)
+        models.append(m)
+        phis.append(phi)
+        params.append(torch.tensor(inputs.vortex_seed(w), device="cuda"))
+        ropts.append(kpm.make_rmft_opts(w.n_target, tol=0.0))
+    mu = torch.zeros(len(cells), dtype=torch.float64, device="cuda")
+    kpm.rmft_iterate_batched(ctx, models, opts, ropts, phis, params, mu, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kpm.rmft_iterate_batched(ctx, models, opts, ropts, phis, params, mu, iters)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / iters
+    seq_ctx = [kpm.kpm_create(0) for _ in cells]
+    mus = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in cells]
+    for k in range(len(cells)):
+        kpm.rmft_iterate(seq_ctx[k], models[k], opts, ropts[k], phis[k], params[k], mus[k], 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        for k in range(len(cells)):
+            kpm.rmft_iterate(seq_ctx[k], models[k], opts, ropts[k], phis[k], params[k], mus[k], 1)
+    torch.cuda.synchronize()
+    ts = (time.perf_counter() - t0) / iters
+    for c in seq_ctx:
+        kpm.kpm_destroy(c)
+    kpm.kpm_destroy(ctx)
+    vm = sum(w.dim for w in cells) * M
+    return {"cells": len(cells), "shapes": sorted({f"{w.nx}x{w.ny}" for w in cells}), "M": M, "precision": "fp32",
+            "s_per_iteration": tb, "vector_moments_per_s": vm / tb,
+            "sequential_s_per_iteration": ts, "sequential_vector_moments_per_s": vm / ts, "speedup": ts / tb}
+
+
+def adjoint_section(kpm, inputs, torch):
+    """64x64 cell, M = 1024, FP32, checkpoints every 32 moments: backward
+    time as a multiple of the forward pass."""
+    w = inputs.CFG4
+    N, M = w.n_sites, w.M
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    opts = kpm.make_opts(M, kpm.KPM_FP32)
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    g = torch.ones(26 * N, dtype=torch.float64, device="cuda")
+    out = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_observables(ctx, model, opts, fields, ab, obs)
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 1.0, out, ckpt_every=32)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    kpm.kpm_observables(ctx, model, opts, fields, ab, obs)
+    e[1].record()
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 1.0, out, ckpt_every=32)
+    e[2].record()
+    torch.cuda.synchronize()
+    tf, tb = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    kpm.kpm_destroy(ctx)
+    return {"cell": "64x64", "M": M, "ckpt_every": 32, "precision": "fp32", "forward_s": tf, "backward_s": tb,
+            "backward_over_forward": tb / tf}
 
 
 def profile_small():

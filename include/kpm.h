@@ -157,6 +157,16 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                  const kpm_rmft_opts* ropts, const double* phi, double* params,
                  double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
 
+/* Autotuner of the recursion launch: times a short pass (M = 32) for every
+ * slab width in {D, 8192, ..., 128} (narrow slabs keep both recursion
+ * vectors in L2) and every column chunk that fits shared memory, and writes
+ * the fastest (block_width, cols_per_block) into *best (other fields copied
+ * from *opts).  Results are cached per (nx, ny, precision) in the context
+ * (a cached answer returns *best_ms_per_step = -1).  fields, ab: device, as
+ * for kpm_observables.  best_ms_per_step: host double or NULL. */
+int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
+                 const double* ab, kpm_opts* best, double* best_ms_per_step, void* stream);
+
 /* Batched self-consistency (cells of uneven size, doping and field): up to
  * n_iter iterations of rmft_iterate's loop for ncell independent cells,
  * replayed as one CUDA graph per iteration.  Cells of equal (nx, ny) share

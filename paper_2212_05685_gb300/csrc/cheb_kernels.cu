@@ -103,9 +103,9 @@ __device__ __forceinline__ void stage_coef(C* dst, const C* __restrict__ table, 
 template <typename Real, int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const typename CT<Real>::C* __restrict__ table,
-                     const typename CT<Real>::C* __restrict__ Vcur, typename CT<Real>::C* __restrict__ Vout,
-                     int64_t s0, double2* __restrict__ acc, const double* __restrict__ am,
-                     const double* __restrict__ ao, int m) {
+                     const typename CT<Real>::C* __restrict__ Vcur, const typename CT<Real>::C* Vprev,
+                     typename CT<Real>::C* Vout, int64_t s0, double2* __restrict__ acc,
+                     const double* __restrict__ am, const double* __restrict__ ao, int m) {
   using C = typename CT<Real>::C;
   using V = typename CT<Real>::V;
   constexpr int VW = CT<Real>::VW;
@@ -127,12 +127,12 @@ __global__ void __launch_bounds__(512, 1)
   // prologue: V_m rows y0-1, y0, y0+1, V_{m-1} row y0, coefficients of y0;
   // then V_m row y0+2, V_{m-1} row y0+1, coefficients of y0+1
   for (int q = 0; q < 3; ++q) stage_row<C, CB>(win + q * rowsz, Vcur, wrapi(y0 - 1 + q, ny), nx, ldv, cb0);
-  if (MODE == 1) stage_row<C, CB>(prev, Vout, y0, nx, ldv, cb0);
+  if (MODE == 1) stage_row<C, CB>(prev, Vprev, y0, nx, ldv, cb0);
   stage_coef<C>(coef, table, y0, nx);
   cp_commit();
   if (nrow >= 2) {
     stage_row<C, CB>(win + 3 * rowsz, Vcur, wrapi(y0 + 2, ny), nx, ldv, cb0);
-    if (MODE == 1) stage_row<C, CB>(prev + rowsz, Vout, y0 + 1, nx, ldv, cb0);
+    if (MODE == 1) stage_row<C, CB>(prev + rowsz, Vprev, y0 + 1, nx, ldv, cb0);
     stage_coef<C>(coef + nx * kCoef, table, y0 + 1, nx);
   }
   cp_commit();
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(512, 1)
     // coefficients of y+2 into the buffers of row y
     if (y + 3 <= y1) stage_row<C, CB>(win + (q & 3) * rowsz, Vcur, wrapi(y + 3, ny), nx, ldv, cb0);
     if (y + 2 < y1) {
-      if (MODE == 1) stage_row<C, CB>(prev + (q & 1) * rowsz, Vout, y + 2, nx, ldv, cb0);
+      if (MODE == 1) stage_row<C, CB>(prev + (q & 1) * rowsz, Vprev, y + 2, nx, ldv, cb0);
       stage_coef<C>(coef + (q & 1) * nx * kCoef, table, y + 2, nx);
     }
     cp_commit();
@@ -280,7 +280,7 @@ __device__ __forceinline__ void acc_term(Acc2& a, float2 c, ulonglong2 u) {
 template <int CB, int MODE>
 __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
                                               const float2* __restrict__ table, const float4* __restrict__ Vcur,
-                                              float4* __restrict__ Vout, int64_t s0, double2* __restrict__ acc,
+                                              const float4* Vprev, float4* Vout, int64_t s0, double2* __restrict__ acc,
                                               const double* __restrict__ am, const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;   // float4 (column pairs) per Nambu row of the chunk
   constexpr int RS = 2 * NV;   // float4 per site of a window row (both Nambu rows)
@@ -333,7 +333,7 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
   ulonglong2 pc[2][2], pn[2][2];
   const ulonglong2 zero2 = make_ulonglong2(0ull, 0ull);
   auto load_prev = [&](int y, ulonglong2 (&dst)[2][2]) {
-    const float4* g = Vout + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
+    const float4* g = Vprev + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
     const int64_t gstep = 2 * (int64_t)xstep * ldq;
     dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
     dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
@@ -447,10 +447,10 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
 template <int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
-                         const float4* __restrict__ Vcur, float4* __restrict__ Vout, int64_t s0,
+                         const float4* __restrict__ Vcur, const float4* Vprev, float4* Vout, int64_t s0,
                          double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
                          int m) {
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vout, s0, acc, am, ao, m);
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, s0, acc, am, ao, m);
 }
 
 // Batched step: cells of one shape, blockIdx.z selects the cell; every cell
@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, i
     cur = reinterpret_cast<const float4*>(b.A[z]);
     out = reinterpret_cast<float4*>(b.B[z]);
   }
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, 0, b.acc[z],
-                          b.am[z], b.ao[z], m);
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out, 0,
+                          b.acc[z], b.am[z], b.ao[z], m);
 }
 
 // V0 = unit vectors e_{s0 + c} (zero elsewhere) and the m = 0 moment terms
@@ -585,27 +585,31 @@ cudaError_t set_smem_f64(int nx) {
 }
 
 template <int CB>
-cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, void* Vout, int64_t s0, double2* acc,
-                       const double* am, const double* ao, int m, int mode, cudaStream_t s) {
+cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, const void* Vprev, void* Vout,
+                       int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
   if (mode == 0)
     cheb_step_f32_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
-                                                                 (const float4*)Vcur, (float4*)Vout, s0, acc, am, ao, m);
+                                                                 (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
+                                                                 s0, acc, am, ao, m);
   else
     cheb_step_f32_kernel<CB, 1><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
-                                                                 (const float4*)Vcur, (float4*)Vout, s0, acc, am, ao, m);
+                                                                 (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
+                                                                 s0, acc, am, ao, m);
   return cudaGetLastError();
 }
 template <int CB>
-cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, void* Vout, int64_t s0, double2* acc,
-                       const double* am, const double* ao, int m, int mode, cudaStream_t s) {
+cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, const void* Vprev, void* Vout,
+                       int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
   if (mode == 0)
     cheb_step_kernel<double, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (double2*)Vout, s0, acc, am, ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, acc, am,
+        ao, m);
   else
     cheb_step_kernel<double, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (double2*)Vout, s0, acc, am, ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, acc, am,
+        ao, m);
   return cudaGetLastError();
 }
 
@@ -692,20 +696,21 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
 
 cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table, const void* Vcur, void* Vout,
                              int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode,
-                             cudaStream_t s) {
+                             cudaStream_t s, const void* Vprev) {
+  if (!Vprev) Vprev = Vout;
   if (precision == KPM_FP32) {
     switch (p.cb) {
-      case 16: return launch_f32<16>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 8: return launch_f32<8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 4: return launch_f32<4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 2: return launch_f32<2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 16: return launch_f32<16>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 8: return launch_f32<8>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 4: return launch_f32<4>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 2: return launch_f32<2>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
     }
   } else {
     switch (p.cb) {
-      case 8: return launch_f64<8>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 4: return launch_f64<4>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 2: return launch_f64<2>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
-      case 1: return launch_f64<1>(p, table, Vcur, Vout, s0, acc, am, ao, m, mode, s);
+      case 8: return launch_f64<8>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 4: return launch_f64<4>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 2: return launch_f64<2>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 1: return launch_f64<1>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
     }
   }
   return cudaErrorInvalidValue;

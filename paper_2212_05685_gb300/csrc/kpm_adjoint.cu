@@ -165,6 +165,74 @@ __global__ void grad_accum_kernel(int nx, int ny, int64_t ldv, int prec, const v
   }
 }
 
+// FP32 slabs: the same sums with the products and the warp reduction in FP32
+// (64 columns per warp, two per lane) and FP64 atomics, so the FP64 pipe
+// (1/64 of the FP32 rate on this part) is used only for the final adds.
+__device__ __forceinline__ float2 pconj2(float4 l, float4 a) {
+  // sum over the pair of columns of l_c conj(a_c); layout (re0, re1, im0, im1)
+  return make_float2(l.x * a.x + l.z * a.z + l.y * a.y + l.w * a.w,
+                     l.z * a.x - l.x * a.z + l.w * a.y - l.y * a.w);
+}
+
+__global__ void grad_accum_f32_kernel(int nx, int ny, int64_t ldv, const float4* __restrict__ lam,
+                                      const float4* __restrict__ alpha, double coef, double2* __restrict__ G) {
+  const int N = nx * ny;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t ldq = ldv / 2;
+  float2 acc[26];
+#pragma unroll
+  for (int k = 0; k < 26; ++k) acc[k] = make_float2(0.f, 0.f);
+  if (i < N) {
+    const int x = i % nx, y = i / nx;
+    int64_t nb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) nb[k] = 2 * (int64_t)(wrapi(x + kNbX[k], nx) + nx * wrapi(y + kNbY[k], ny)) * ldq;
+    const int64_t r0 = 2 * (int64_t)i * ldq;
+    // each lane sums its column pairs over the whole slab in FP32 registers
+    for (int64_t q = (int64_t)blockIdx.y * 32 + lane; q < ldq; q += (int64_t)gridDim.y * 32) {
+      const float4 l0 = lam[r0 + q];
+      const float4 l1 = lam[r0 + ldq + q];
+      const float2 d0 = pconj2(l0, alpha[r0 + q]);
+      const float2 d1 = pconj2(l1, alpha[r0 + ldq + q]);
+      acc[0].x += d0.x;
+      acc[0].y += d0.y;
+      acc[13].x += d1.x;
+      acc[13].y += d1.y;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 a0 = alpha[nb[k] + q];
+        const float4 a1 = alpha[nb[k] + ldq + q];
+        const float2 h0 = pconj2(l0, a0), h1 = pconj2(l1, a1);
+        acc[1 + k].x += h0.x;
+        acc[1 + k].y += h0.y;
+        acc[14 + k].x += h1.x;
+        acc[14 + k].y += h1.y;
+        if (k < 4) {
+          const float2 p0 = pconj2(l0, a1), p1 = pconj2(l1, a0);
+          acc[9 + k].x += p0.x;
+          acc[9 + k].y += p0.y;
+          acc[22 + k].x += p1.x;
+          acc[22 + k].y += p1.y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 26; ++k) {
+    float re = acc[k].x, im = acc[k].y;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0 && i < N && (re != 0.f || im != 0.f)) {
+      double2* g = G + (size_t)(2 * i + (k >= 13)) * 13 + (k % 13);
+      atomicAdd(&g->x, coef * (double)re);
+      atomicAdd(&g->y, coef * (double)im);
+    }
+  }
+}
+
 // dL/d(eps, T, D) from G (gradient in h~), divided by a (h~ = (h - b)/a).
 //   stencil slots of row I: 0 diag, 1..8 hops to (+1,0) (-1,0) (0,+1) (0,-1)
 //   (+1,+1) (-1,-1) (+1,-1) (-1,+1), 9..12 pairings to (+1,0) (-1,0) (0,+1) (0,-1)
@@ -229,6 +297,14 @@ cudaError_t launch_seed_scatter(const ChebPlan& p, int prec, void* lam, int64_t 
 cudaError_t launch_grad_accum(const ChebPlan& p, int prec, const void* lam, const void* alpha, double coef,
                               double2* G, cudaStream_t s) {
   const int N = p.nx * p.ny;
+  if (prec == KPM_FP32) {
+    // a few column groups per site: enough CTAs for the GPU, few atomics per entry
+    const int64_t groups = (p.ldv / 2 + 31) / 32;
+    const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(groups, std::max<int64_t>(1, 8 * 152 * 8 / std::max(N, 1))));
+    const dim3 grid((N + 7) / 8, (unsigned)gy);
+    grad_accum_f32_kernel<<<grid, 256, 0, s>>>(p.nx, p.ny, p.ldv, (const float4*)lam, (const float4*)alpha, coef, G);
+    return cudaGetLastError();
+  }
   const dim3 grid((N + kGradSites - 1) / kGradSites, (unsigned)((p.ldv + kGradCols - 1) / kGradCols));
   grad_accum_kernel<<<grid, kGradSites * kGradCols, 0, s>>>(p.nx, p.ny, p.ldv, prec, lam, alpha, coef, G);
   return cudaGetLastError();

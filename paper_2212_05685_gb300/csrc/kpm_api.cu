@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -73,6 +74,9 @@ struct kpm_ctx {
   size_t bhost_n = 0;
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
+
+  // autotuned (block_width, cols_per_block) per (nx, ny, precision)
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -627,43 +631,50 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const double* ao = ctx->ao;
 
   for (int64_t s0 = 0; s0 < D && M >= 2; s0 += pp.width) {
-    // forward with checkpoints (alpha_{k seg}, alpha_{k seg + 1})
-    KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, am, ao, s));
-    KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, nullptr, am, ao, 0, 0, s));
-    KPM_CU(cudaMemcpyAsync(ckpt(0), A, vbytes, cudaMemcpyDeviceToDevice, s));
-    KPM_CU(cudaMemcpyAsync(ckpt(1), B, vbytes, cudaMemcpyDeviceToDevice, s));
+    // forward, writing the checkpointed vectors (alpha_{k seg}, alpha_{k seg + 1})
+    // in place and stepping through the two temporaries otherwise
+    auto ckpt_slot = [&](int idx) -> void* {
+      if (idx % seg == 0 && idx / seg < K) return ckpt(2 * (idx / seg));
+      if (idx % seg == 1 && idx / seg < K) return ckpt(2 * (idx / seg) + 1);
+      return nullptr;
+    };
+    KPM_CU(launch_cheb_init(p, prec, ckpt(0), s0, ctx->acc, am, ao, s));
+    KPM_CU(launch_cheb_step(p, prec, ctx->table, ckpt(0), ckpt(1), s0, nullptr, am, ao, 0, 0, s));
+    const void* a_prev = ckpt(0);
+    const void* a_cur = ckpt(1);
     const int last_needed = (K - 1) * seg + 1;  // highest checkpointed index
     for (int mm = 1; mm + 1 <= last_needed; ++mm) {
-      const void* cur = (mm & 1) ? B : A;
-      void* out = (mm & 1) ? A : B;  // becomes alpha_{mm+1}
-      KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, nullptr, am, ao, mm, 1, s));
-      const int idx = mm + 1;
-      if (idx % seg == 0 && idx / seg < K)
-        KPM_CU(cudaMemcpyAsync(ckpt(2 * (idx / seg)), out, vbytes, cudaMemcpyDeviceToDevice, s));
-      if (idx % seg == 1 && idx / seg < K)
-        KPM_CU(cudaMemcpyAsync(ckpt(2 * (idx / seg) + 1), out, vbytes, cudaMemcpyDeviceToDevice, s));
+      void* dest = ckpt_slot(mm + 1);
+      if (!dest) {
+        if (a_prev == A || a_prev == B) dest = const_cast<void*>(a_prev);  // in place over alpha_{mm-1}
+        else dest = (a_cur == A) ? B : A;
+      }
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, a_cur, dest, s0, nullptr, am, ao, mm, 1, s, a_prev));
+      a_prev = a_cur;
+      a_cur = dest;
     }
-    // backward: lambda_{m+1} in `cur`, lambda_{m+2} in `nxt`, both zero above M-1
+    // backward: lambda_{m+1} in `lcur`, lambda_{m+2} in `lnxt`, both zero above M-1
     void* lcur = lamA;
     void* lnxt = lamB;
     KPM_CU(cudaMemsetAsync(lcur, 0, vbytes, s));
     KPM_CU(cudaMemsetAsync(lnxt, 0, vbytes, s));
+    std::vector<const void*> segp(seg);
     for (int k = K - 1; k >= 0; --k) {
       const int m_hi = std::min((k + 1) * seg, M - 1);
       const int m_lo = k * seg + 1;
-      // recompute alpha_{k seg} .. alpha_{m_hi - 1} into the segment buffer
-      const int nseg = m_hi - 1 - k * seg + 1;
-      KPM_CU(cudaMemcpyAsync(segv(0), ckpt(2 * k), vbytes, cudaMemcpyDeviceToDevice, s));
-      if (nseg > 1) KPM_CU(cudaMemcpyAsync(segv(1), ckpt(2 * k + 1), vbytes, cudaMemcpyDeviceToDevice, s));
+      // alpha_{k seg} .. alpha_{m_hi - 1}: two checkpoints, then out-of-place steps
+      const int nseg = m_hi - k * seg;
+      segp[0] = ckpt(2 * k);
+      if (nseg > 1) segp[1] = ckpt(2 * k + 1);
       for (int j = 2; j < nseg; ++j) {
-        KPM_CU(cudaMemcpyAsync(segv(j), segv(j - 2), vbytes, cudaMemcpyDeviceToDevice, s));
-        KPM_CU(launch_cheb_step(p, prec, ctx->table, segv(j - 1), segv(j), s0, nullptr, am, ao, 0, 1, s));
+        KPM_CU(launch_cheb_step(p, prec, ctx->table, segp[j - 1], segv(j), s0, nullptr, am, ao, 0, 1, s, segp[j - 2]));
+        segp[j] = segv(j);
       }
       for (int m = m_hi; m >= m_lo; --m) {
         // lnxt <- 2 h~ lambda_{m+1} - lambda_{m+2} + c_m = lambda_m
         KPM_CU(launch_cheb_step(p, prec, ctx->table, lcur, lnxt, s0, nullptr, am, ao, 0, 1, s));
         KPM_CU(launch_seed_scatter(p, prec, lnxt, s0, ctx->wseed, am, ao, m, s));
-        KPM_CU(launch_grad_accum(p, prec, lnxt, segv(m - 1 - k * seg), m == 1 ? 1.0 : 2.0, ctx->Gacc, s));
+        KPM_CU(launch_grad_accum(p, prec, lnxt, segp[m - 1 - k * seg], m == 1 ? 1.0 : 2.0, ctx->Gacc, s));
         std::swap(lcur, lnxt);
       }
     }
@@ -926,6 +937,78 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
   }
   if (stats) memcpy(stats, st.data(), sizeof(kpm_rmft_stats) * ncell);
   return status;
+}
+
+
+int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields, const double* ab,
+                 kpm_opts* best, double* best_ms_per_step, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, fields, "fields")) || (r = check_dev(ctx, ab, "ab"))) return r;
+  if (!opts || !best) return fail(ctx, KPM_EINVAL, "null argument");
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  const int64_t D = 2 * (int64_t)N;
+  const int prec = opts->precision;
+  *best = *opts;
+  auto key = std::make_tuple(model->nx, model->ny, prec);
+  auto hit = ctx->tuned.find(key);
+  if (hit != ctx->tuned.end()) {
+    best->block_width = hit->second.first;
+    best->cols_per_block = hit->second.second;
+    if (best_ms_per_step) *best_ms_per_step = -1.0;
+    return KPM_OK;
+  }
+  if ((r = ensure_site_scratch(ctx, N))) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  KPM_CU(cudaEventCreate(&e0));
+  KPM_CU(cudaEventCreate(&e1));
+  // candidates: full width and narrower slabs (down to L2-resident ones), every column chunk
+  std::vector<int64_t> widths = {D};
+  for (int64_t w : {8192, 4096, 2048, 1024, 512, 384, 256, 128})
+    if (w < D) widths.push_back(w);
+  std::vector<int> cols = prec == KPM_FP32 ? std::vector<int>{16, 8, 4} : std::vector<int>{8, 4, 2};
+  const int Mt = 32;  // trial order: init/gather amortised, well under a second per trial at 10^4 sites
+  double best_t = 1e300;
+  int best_w = 0, best_c = 0;
+  for (int64_t w : widths) {
+    for (int c : cols) {
+      kpm_opts o = *opts;
+      o.M = Mt;
+      o.block_width = (int)std::min<int64_t>(w, D);
+      o.cols_per_block = c;
+      PassPlan pp;
+      if (plan_pass(ctx, model, &o, &pp) != KPM_OK) continue;
+      if (pp.cheb.cb != c) continue;  // chunk does not fit for this lattice
+      if ((r = ensure_pass_scratch(ctx, model, &o, pp))) break;
+      // one warm-up pass, one timed
+      if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
+      KPM_CU(cudaEventRecord(e0, s));
+      if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
+      KPM_CU(cudaEventRecord(e1, s));
+      KPM_CU(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      KPM_CU(cudaEventElapsedTime(&ms, e0, e1));
+      const double per_step = ms / (Mt - 1);
+      if (per_step < best_t) {
+        best_t = per_step;
+        best_w = o.block_width;
+        best_c = c;
+      }
+    }
+    if (r) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r) return r;
+  if (best_c == 0) return fail(ctx, KPM_EINVAL, "no recursion configuration fits this lattice");
+  ctx->tuned[key] = std::make_pair(best_w, best_c);
+  best->block_width = best_w;
+  best->cols_per_block = best_c;
+  if (best_ms_per_step) *best_ms_per_step = best_t;
+  return KPM_OK;
 }
 
 }  // extern "C"

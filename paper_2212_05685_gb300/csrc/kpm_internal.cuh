@@ -71,11 +71,12 @@ cudaError_t cheb_prepare(const ChebPlan& p, int precision);
 // zero V0/acc slab, V0 = unit vectors of columns [s0, s0 + b), acc init with a_0 terms
 cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t s0,
                              double2* acc, const double* am, const double* ao, cudaStream_t s);
-// one recursion step. mode 0: Vout = h~ Vcur (first step); mode 1: Vout = 2h~ Vcur - Vout,
-// accumulating a_m Vcur into acc (m = step index of Vcur)
+// one recursion step. mode 0: Vout = h~ Vcur (first step); mode 1: Vout = 2h~ Vcur - Vprev
+// (Vprev = nullptr: in place, Vprev = Vout), accumulating a_m Vcur into acc unless acc is null
+// (m = step index of Vcur)
 cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table, const void* Vcur,
                              void* Vout, int64_t s0, double2* acc, const double* am,
-                             const double* ao, int m, int mode, cudaStream_t s);
+                             const double* ao, int m, int mode, cudaStream_t s, const void* Vprev = nullptr);
 // batched FP32 step over ncell cells of one shape (plan p, full-width slabs)
 cudaError_t cheb_prepare_batched(const ChebPlan& p);
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,

@@ -65,6 +65,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
     "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
                                                _P, _P]),
+    "kpm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P,
+                                    ctypes.POINTER(kpm_opts), ctypes.POINTER(ctypes.c_double), _P]),
     "rmft_iterate_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts),
                                             ctypes.POINTER(kpm_rmft_opts), ctypes.POINTER(ctypes.c_void_p),
                                             ctypes.POINTER(ctypes.c_void_p), _P, ctypes.c_int,
@@ -205,6 +207,15 @@ def rmft_iterate(ctx: Context, model, opts, ropts, phi, params, mu_eff, n_iter, 
     if check:
         ctx.check(st, "rmft_iterate")
     return st, stats
+
+
+def kpm_autotune(ctx: Context, model, opts, fields, ab, stream=None):
+    """Returns (best kpm_opts, ms per recursion step or -1 when cached)."""
+    best = kpm_opts()
+    ms = ctypes.c_double()
+    ctx.check(ctx.lib.kpm_autotune(ctx.handle, ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
+                                   ctypes.byref(best), ctypes.byref(ms), _stream(stream)), "kpm_autotune")
+    return best, ms.value
 
 
 def rmft_iterate_batched(ctx: Context, models, opts, ropts, phis, params, mu_eff, n_iter, stream=None, check=True):
