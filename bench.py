@@ -375,6 +375,7 @@ def run_ours(args):
 
     batched = None if args.no_batched else batched_section(kpm, inputs, torch)
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
+    precision = precision_section(kpm, inputs, torch)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -405,6 +406,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "fp64": fp64,
+        "fp32_error": precision,
         "batched": batched,
         "adjoint": adjoint,
         "residual_last": last.residual if last else None,
@@ -458,6 +460,32 @@ def batched_section(kpm, inputs, torch, iters=3):
     return {"cells": len(cells), "shapes": sorted({f"{w.nx}x{w.ny}" for w in cells}), "M": M, "precision": "fp32",
             "s_per_iteration": tb, "vector_moments_per_s": vm / tb,
             "sequential_s_per_iteration": ts, "sequential_vector_moments_per_s": vm / ts, "speedup": ts / tb}
+
+
+def precision_section(kpm, inputs, torch):
+    """FP32 recursion error against the FP64 recursion, per observable, on the
+    48 x 24 cell (D = 2304, M = 1024) at its seeded order parameters."""
+    w = inputs.CFG1
+    N = w.n_sites
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 1.7, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    out = {}
+    for name, prec in (("fp64", kpm.KPM_FP64), ("fp32", kpm.KPM_FP32)):
+        obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        kpm.kpm_observables(ctx, model, kpm.make_opts(w.M, prec), fields, ab, obs)
+        out[name] = obs
+    torch.cuda.synchronize()
+    d = (out["fp32"] - out["fp64"]).abs()
+    kpm.kpm_destroy(ctx)
+    return {"cell": "48x24", "M": w.M, "max_err_n": float(d[:2 * N].max()), "max_err_chi": float(d[2 * N:18 * N].max()),
+            "max_err_F": float(d[18 * N:].max()), "bound": 2e-5}
 
 
 def adjoint_section(kpm, inputs, torch):
