@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
+                    help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
     return ap.parse_args()
@@ -522,6 +524,38 @@ def adjoint_section(kpm, inputs, torch):
             "backward_over_forward": tb / tf}
 
 
+def profile_adjoint(full=False):
+    """Adjoint case for ncu: the 64x64 cell, FP32.  Small (default): M = 64,
+    checkpoints every 8 moments, slabs of 2048 columns (134 MB per slab
+    vector, 3.5 GB of adjoint scratch).  full: the benchmarked backward pass
+    (M = 1024, checkpoints every 32, library-chosen slab width), once."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    w = inputs.CFG4
+    N = w.n_sites
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    g = torch.ones(26 * N, dtype=torch.float64, device="cuda")
+    out = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    if full:
+        kpm.kpm_backward(ctx, model, kpm.make_opts(w.M, kpm.KPM_FP32), fields, ab, g, 1.0, out, ckpt_every=32)
+    else:
+        kpm.kpm_backward(ctx, model, kpm.make_opts(64, kpm.KPM_FP32, 2048), fields, ab, g, 1.0, out, ckpt_every=8)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out).all())
+    kpm.kpm_destroy(ctx)
+    print("profile-adjoint done")
+    return 0
+
+
 def profile_small():
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
     (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
@@ -552,6 +586,8 @@ def main():
     args = parse()
     if args.profile_small:
         return profile_small()
+    if args.profile_adjoint:
+        return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

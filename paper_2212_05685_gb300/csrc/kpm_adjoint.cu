@@ -8,8 +8,8 @@
 // over the 13 stencil entries (I, K) of every row (h~ is Hermitian, so the
 // lambda recursion is the forward stencil SpMM).  The lambda steps reuse the
 // recursion kernel; this file holds the seed scatter, the stencil-entry
-// accumulation of G (FP64, one atomic per entry and CTA after a warp
-// reduction) and the chain from G to the fields (eps, T, D).
+// accumulation of G (FP32 or FP64 products, FP64 per-warp partial sums without
+// atomics) and the chain from G to the fields (eps, T, D).
 #include <algorithm>
 
 #include "kpm_internal.cuh"
@@ -33,14 +33,6 @@ __constant__ int kSlotFlip[kSlots] = {0, 0, 0, 0, 0, 1, 1, 1, 1, 0};
 __constant__ int kNbX[8] = {1, -1, 0, 0, 1, -1, 1, -1};
 __constant__ int kNbY[8] = {0, 0, 1, -1, 1, -1, -1, 1};
 
-// element (K, c) of a slab, any precision/layout
-__device__ __forceinline__ double2 slab_elem(const void* V, int prec, int64_t ldv, int64_t K, int64_t c) {
-  if (prec == KPM_FP32) {
-    const float4 q = reinterpret_cast<const float4*>(V)[K * (ldv / 2) + (c >> 1)];
-    return (c & 1) ? make_double2(q.y, q.w) : make_double2(q.x, q.z);
-  }
-  return reinterpret_cast<const double2*>(V)[K * ldv + c];
-}
 __device__ __forceinline__ void slab_add(void* V, int prec, int64_t ldv, int64_t K, int64_t c, double re, double im) {
   if (prec == KPM_FP32) {
     float* q = reinterpret_cast<float*>(reinterpret_cast<float4*>(V) + K * (ldv / 2) + (c >> 1));
@@ -107,129 +99,247 @@ __global__ void seed_scatter_kernel(int nx, int ny, int64_t D, int64_t ldv, int6
   }
 }
 
-// G[I][k] += coef * sum_{c in slab} lam[I, c] conj(alpha[K_k(I), c]) for the
-// 13 stencil entries of both Nambu rows of every site.  One warp per site
-// and 32 columns: the products are reduced across the warp by shuffles, then
-// one FP64 atomic per entry and warp.
-constexpr int kGradCols = 32;  // columns per block
-constexpr int kGradSites = 8;  // sites per block
+// Stencil-entry sums of the adjoint:
+//   G[I][t] += coef * sum_{c in slab} lam[I, c] conj(alpha[K_t(I), c])
+// for the 13 entries t of every row I (t = 0 the diagonal, 1..8 the hops to
+// the same Nambu row of the neighbours (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1)
+// (-1,-1) (+1,-1) (-1,+1), 9..12 the pairings to the other Nambu row of the
+// four nearest neighbours).  The slab's columns are dealt to `groups` sets;
+// exactly one warp (FP64) or CTA (FP32) adds the set's sum for a given row
+// to P[set][I][t], so the sums are deterministic (fixed order within a
+// launch, launches in stream order); the sets are added in fixed order at
+// the end (grad_reduce_kernel).
+//
+// FP64 slabs (interleaved complex): one warp owns one (row, set), its lanes
+// stride over the set's columns with all 13 alpha rows loaded before the
+// products, and lane t adds the warp's sum for entry t.  The FP64 path is
+// bound by the FP64 pipe, not by these loads.
+constexpr int kGradRows = 8;  // warps (rows) per CTA
 
-__global__ void grad_accum_kernel(int nx, int ny, int64_t ldv, int prec, const void* __restrict__ lam,
-                                  const void* __restrict__ alpha, double coef, double2* __restrict__ G) {
-  const int N = nx * ny;
-  const int tc = threadIdx.x % kGradCols;
-  const int ts = threadIdx.x / kGradCols;
-  const int i = blockIdx.x * kGradSites + ts;
-  const int64_t c = (int64_t)blockIdx.y * kGradCols + tc;
-  double2 acc[26];
-#pragma unroll
-  for (int k = 0; k < 26; ++k) acc[k] = make_double2(0.0, 0.0);
-  if (i < N && c < ldv) {
-    const int x = i % nx, y = i / nx;
-    const double2 l0 = slab_elem(lam, prec, ldv, 2 * (int64_t)i, c);
-    const double2 l1 = slab_elem(lam, prec, ldv, 2 * (int64_t)i + 1, c);
-    // diagonal
-    {
-      const double2 a0 = slab_elem(alpha, prec, ldv, 2 * (int64_t)i, c);
-      const double2 a1 = slab_elem(alpha, prec, ldv, 2 * (int64_t)i + 1, c);
-      acc[0] = make_double2(l0.x * a0.x + l0.y * a0.y, l0.y * a0.x - l0.x * a0.y);
-      acc[13] = make_double2(l1.x * a1.x + l1.y * a1.y, l1.y * a1.x - l1.x * a1.y);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int j = wrapi(x + kNbX[k], nx) + nx * wrapi(y + kNbY[k], ny);
-      const double2 a0 = slab_elem(alpha, prec, ldv, 2 * (int64_t)j, c);
-      const double2 a1 = slab_elem(alpha, prec, ldv, 2 * (int64_t)j + 1, c);
-      // hops: (i,0)->(j,0), (i,1)->(j,1)
-      acc[1 + k] = make_double2(l0.x * a0.x + l0.y * a0.y, l0.y * a0.x - l0.x * a0.y);
-      acc[14 + k] = make_double2(l1.x * a1.x + l1.y * a1.y, l1.y * a1.x - l1.x * a1.y);
-      if (k < 4) {  // pairings: (i,0)->(j,1), (i,1)->(j,0)
-        acc[9 + k] = make_double2(l0.x * a1.x + l0.y * a1.y, l0.y * a1.x - l0.x * a1.y);
-        acc[22 + k] = make_double2(l1.x * a0.x + l1.y * a0.y, l1.y * a0.x - l1.x * a0.y);
-      }
-    }
-  }
-  // reduce over the 32 columns of this site (one warp = one site)
-#pragma unroll
-  for (int k = 0; k < 26; ++k) {
-    double re = acc[k].x, im = acc[k].y;
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_down_sync(0xffffffffu, re, o);
-      im += __shfl_down_sync(0xffffffffu, im, o);
-    }
-    if (tc == 0 && i < N && (re != 0.0 || im != 0.0)) {
-      double2* g = G + (size_t)(2 * i + (k >= 13)) * 13 + (k % 13);
-      atomicAdd(&g->x, coef * re);
-      atomicAdd(&g->y, coef * im);
-    }
-  }
-}
-
-// FP32 slabs: the same sums with the products and the warp reduction in FP32
-// (64 columns per warp, two per lane) and FP64 atomics, so the FP64 pipe
-// (1/64 of the FP32 rate on this part) is used only for the final adds.
-__device__ __forceinline__ float2 pconj2(float4 l, float4 a) {
-  // sum over the pair of columns of l_c conj(a_c); layout (re0, re1, im0, im1)
-  return make_float2(l.x * a.x + l.z * a.z + l.y * a.y + l.w * a.w,
-                     l.z * a.x - l.x * a.z + l.w * a.y - l.y * a.w);
-}
-
-__global__ void grad_accum_f32_kernel(int nx, int ny, int64_t ldv, const float4* __restrict__ lam,
-                                      const float4* __restrict__ alpha, double coef, double2* __restrict__ G) {
-  const int N = nx * ny;
+__global__ void __launch_bounds__(kGradRows * 32, 2)
+grad_rows_f64_kernel(int nx, int ny, int64_t ldv, const double2* __restrict__ lam,
+                     const double2* __restrict__ alpha, double coef, double2* __restrict__ P) {
+  const int64_t D = 2 * (int64_t)nx * ny;
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t ldq = ldv / 2;
+  const int64_t R = (int64_t)blockIdx.x * kGradRows + (threadIdx.x >> 5);
+  if (R >= D) return;  // uniform per warp; the kernel has no block barrier
+  const int groups = gridDim.y;
+  const int i = (int)(R >> 1), r = (int)(R & 1);
+  const int x = i % nx, y = i / nx;
+  const double2* rows[13];
+  rows[0] = alpha + R * ldv;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int64_t j = wrapi(x + kNbX[k], nx) + (int64_t)nx * wrapi(y + kNbY[k], ny);
+    rows[1 + k] = alpha + (2 * j + r) * ldv;
+    if (k < 4) rows[9 + k] = alpha + (2 * j + 1 - r) * ldv;
+  }
+  const double2* lrow = lam + R * ldv;
+  double2 acc[13];
+#pragma unroll
+  for (int t = 0; t < 13; ++t) acc[t] = make_double2(0.0, 0.0);
+  for (int64_t c = (int64_t)blockIdx.y * 32 + lane; c < ldv; c += (int64_t)groups * 32) {
+    const double2 l = lrow[c];
+    double2 v[13];
+#pragma unroll
+    for (int t = 0; t < 13; ++t) v[t] = rows[t][c];
+#pragma unroll
+    for (int t = 0; t < 13; ++t) {
+      acc[t].x += l.x * v[t].x + l.y * v[t].y;
+      acc[t].y += l.y * v[t].x - l.x * v[t].y;
+    }
+  }
+  double2 mine = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int t = 0; t < 13; ++t) {
+    double re = acc[t].x, im = acc[t].y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == t) mine = make_double2(re, im);
+  }
+  if (lane < 13) {
+    double2* e = P + ((int64_t)blockIdx.y * D + R) * 13 + lane;
+    e->x += coef * mine.x;
+    e->y += coef * mine.y;
+  }
+}
+
+// FP32 slabs: a tile of kTX x kTY sites per CTA, both Nambu rows, one lane per
+// site.  Column pairs stream through shared memory kQ at a time (two stages
+// in flight through cp.async): the alpha rows of the tile and its one-site
+// halo (every alpha row is fetched once per tile instead of once per stencil
+// entry) and the tile's own lambda rows.  Each lane keeps its 26 sums in FP32
+// registers across every column pair its CTA visits, so no cross-lane
+// reduction runs inside the loop; the two halves of the CTA take alternate
+// pairs of a stage and are combined once at the end.  Column blocks are dealt
+// to `groups` CTAs per tile; CTA (tile, set) is the only writer of
+// P[set][rows of the tile][*].
+constexpr int kTX = 16, kTY = 8, kQ = 8;
+constexpr int kTileSites = kTX * kTY;                   // 128 lanes per half
+constexpr int kHX = kTX + 2, kHY = kTY + 2;
+constexpr int kSA = (kHX * kHY) | 1;                   // odd strides: conflict-free
+constexpr int kSL = kTileSites | 1;                     //   16-byte shared accesses
+constexpr int kStage = 2 * kQ * kSA + 2 * kQ * kSL;     // float4 per stage
+constexpr size_t kTileSmem = 2 * kStage * sizeof(float4);
+constexpr int kTileThreads = 2 * kTileSites;
+
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_group0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Copy plan of one thread, the same for every stage: thread t copies pair
+// q = t % kQ of the rows it owns (kQ divides the block size), so only the
+// row and the shared-memory slot vary across its items.
+constexpr int kAItems = (kHX * kHY * 2 * kQ + kTileThreads - 1) / kTileThreads;
+constexpr int kLItems = (kTileSites * 2 * kQ) / kTileThreads;
+static_assert(kTileThreads % kQ == 0 && (kTileSites * 2 * kQ) % kTileThreads == 0, "copy plan");
+
+struct TileCopyPlan {
+  int arow[kAItems], aslot[kAItems];  // alpha halo rows (arow < 0: no item)
+  int lrow[kLItems], lslot[kLItems];  // lambda rows of the tile (lrow < 0: outside the lattice)
+};
+
+__device__ __forceinline__ void tile_copy_plan(TileCopyPlan& c, int nx, int ny, int x0, int y0) {
+  const int q = threadIdx.x % kQ;
+#pragma unroll
+  for (int k = 0; k < kAItems; ++k) {
+    const int it = threadIdx.x + k * kTileThreads;
+    const int rn = it / kQ, n = rn & 1, h = rn >> 1;
+    c.arow[k] = -1;
+    c.aslot[k] = 0;
+    if (it < kHX * kHY * 2 * kQ) {
+      const int gx = wrapi(x0 - 1 + h % kHX, nx), gy = wrapi(y0 - 1 + h / kHX, ny);
+      c.arow[k] = 2 * (gy * nx + gx) + n;
+      c.aslot[k] = (n * kQ + q) * kSA + h;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kLItems; ++k) {
+    const int it = threadIdx.x + k * kTileThreads;
+    const int rn = it / kQ, n = rn & 1, t = rn >> 1;
+    const int sx = x0 + t % kTX, sy = y0 + t / kTX;
+    c.lrow[k] = (sx < nx && sy < ny) ? 2 * (sy * nx + sx) + n : -1;
+    c.lslot[k] = (n * kQ + q) * kSL + t;
+  }
+}
+
+__device__ __forceinline__ void grad_tile_load(float4* stage, const TileCopyPlan& c, int64_t ldq, int64_t p0,
+                                               const float4* __restrict__ lam, const float4* __restrict__ alpha) {
+  float4* sa = stage;
+  float4* sl = stage + 2 * kQ * kSA;
+  const int64_t pq = p0 + threadIdx.x % kQ;
+  const bool inq = pq < ldq;
+  const int64_t pc = inq ? pq : 0;
+#pragma unroll
+  for (int k = 0; k < kAItems; ++k)
+    if (c.arow[k] >= 0) cp_async16_zfill(sa + c.aslot[k], alpha + (int64_t)c.arow[k] * ldq + pc, inq ? 16 : 0);
+#pragma unroll
+  for (int k = 0; k < kLItems; ++k) {
+    const bool ok = inq && c.lrow[k] >= 0;
+    cp_async16_zfill(sl + c.lslot[k], lam + (ok ? (int64_t)c.lrow[k] * ldq + pc : 0), ok ? 16 : 0);
+  }
+  cp_commit_group();
+}
+
+__device__ __forceinline__ void pmac(float2& a, const float4& l, const float4& v) {
+  a.x += l.x * v.x + l.z * v.z + l.y * v.y + l.w * v.w;
+  a.y += l.z * v.x - l.x * v.z + l.w * v.y - l.y * v.w;
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1)
+grad_tile_f32_kernel(int nx, int ny, int64_t ldq, int tiles_x, const float4* __restrict__ lam,
+                     const float4* __restrict__ alpha, double coef, double2* __restrict__ P) {
+  extern __shared__ float4 gsm[];
+  const int64_t D = 2 * (int64_t)nx * ny;
+  const int x0 = (blockIdx.x % tiles_x) * kTX, y0 = (blockIdx.x / tiles_x) * kTY;
+  const int groups = gridDim.y;
+  const int64_t nblk = (ldq + kQ - 1) / kQ;
+  const int half = threadIdx.x / kTileSites;
+  const int ls = threadIdx.x % kTileSites;
+  const int tx = ls % kTX, ty = ls / kTX;
+  const bool valid = x0 + tx < nx && y0 + ty < ny;
+  const int hc = (ty + 1) * kHX + tx + 1;
   float2 acc[26];
 #pragma unroll
-  for (int k = 0; k < 26; ++k) acc[k] = make_float2(0.f, 0.f);
-  if (i < N) {
-    const int x = i % nx, y = i / nx;
-    int64_t nb[8];
+  for (int t = 0; t < 26; ++t) acc[t] = make_float2(0.f, 0.f);
+  TileCopyPlan cp;
+  tile_copy_plan(cp, nx, ny, x0, y0);
+
+  int buf = 0;
+  int64_t blk = blockIdx.y;
+  if (blk < nblk) grad_tile_load(gsm, cp, ldq, blk * kQ, lam, alpha);
+  for (; blk < nblk; blk += groups) {
+    const int64_t nxt = blk + groups;
+    if (nxt < nblk) {
+      grad_tile_load(gsm + (buf ^ 1) * kStage, cp, ldq, nxt * kQ, lam, alpha);
+      cp_wait_group1();
+    } else {
+      cp_wait_group0();
+    }
+    __syncthreads();
+    if (valid) {
+      const float4* sa = gsm + buf * kStage;
+      const float4* sl = sa + 2 * kQ * kSA;
+#pragma unroll 2
+      for (int q = half; q < kQ; q += 2) {
+        const float4* a0r = sa + q * kSA;          // Nambu row 0 of the halo at pair q
+        const float4* a1r = sa + (kQ + q) * kSA;   // Nambu row 1
+        const float4 l0 = sl[q * kSL + ls];
+        const float4 l1 = sl[(kQ + q) * kSL + ls];
+        pmac(acc[0], l0, a0r[hc]);
+        pmac(acc[13], l1, a1r[hc]);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) nb[k] = 2 * (int64_t)(wrapi(x + kNbX[k], nx) + nx * wrapi(y + kNbY[k], ny)) * ldq;
-    const int64_t r0 = 2 * (int64_t)i * ldq;
-    // each lane sums its column pairs over the whole slab in FP32 registers
-    for (int64_t q = (int64_t)blockIdx.y * 32 + lane; q < ldq; q += (int64_t)gridDim.y * 32) {
-      const float4 l0 = lam[r0 + q];
-      const float4 l1 = lam[r0 + ldq + q];
-      const float2 d0 = pconj2(l0, alpha[r0 + q]);
-      const float2 d1 = pconj2(l1, alpha[r0 + ldq + q]);
-      acc[0].x += d0.x;
-      acc[0].y += d0.y;
-      acc[13].x += d1.x;
-      acc[13].y += d1.y;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float4 a0 = alpha[nb[k] + q];
-        const float4 a1 = alpha[nb[k] + ldq + q];
-        const float2 h0 = pconj2(l0, a0), h1 = pconj2(l1, a1);
-        acc[1 + k].x += h0.x;
-        acc[1 + k].y += h0.y;
-        acc[14 + k].x += h1.x;
-        acc[14 + k].y += h1.y;
-        if (k < 4) {
-          const float2 p0 = pconj2(l0, a1), p1 = pconj2(l1, a0);
-          acc[9 + k].x += p0.x;
-          acc[9 + k].y += p0.y;
-          acc[22 + k].x += p1.x;
-          acc[22 + k].y += p1.y;
+        for (int k = 0; k < 8; ++k) {
+          const int hk = hc + kNbY[k] * kHX + kNbX[k];
+          const float4 b0 = a0r[hk], b1 = a1r[hk];
+          pmac(acc[1 + k], l0, b0);
+          pmac(acc[14 + k], l1, b1);
+          if (k < 4) {
+            pmac(acc[9 + k], l0, b1);
+            pmac(acc[22 + k], l1, b0);
+          }
         }
       }
     }
+    __syncthreads();  // the next iteration's copies overwrite this stage
+    buf ^= 1;
   }
+  // combine the two halves (shared memory is free again) and add to P
+  float2* red = reinterpret_cast<float2*>(gsm);
+  if (half == 1) {
 #pragma unroll
-  for (int k = 0; k < 26; ++k) {
-    float re = acc[k].x, im = acc[k].y;
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_down_sync(0xffffffffu, re, o);
-      im += __shfl_down_sync(0xffffffffu, im, o);
+    for (int t = 0; t < 26; ++t) red[t * kTileSites + ls] = acc[t];
+  }
+  __syncthreads();
+  if (half == 0 && valid) {
+    const int64_t site = (int64_t)(y0 + ty) * nx + x0 + tx;
+#pragma unroll
+    for (int t = 0; t < 26; ++t) {
+      const float2 o = red[t * kTileSites + ls];
+      double2* e = P + ((int64_t)blockIdx.y * D + 2 * site + (t >= 13)) * 13 + (t % 13);
+      e->x += coef * ((double)acc[t].x + (double)o.x);
+      e->y += coef * ((double)acc[t].y + (double)o.y);
     }
-    if (lane == 0 && i < N && (re != 0.f || im != 0.f)) {
-      double2* g = G + (size_t)(2 * i + (k >= 13)) * 13 + (k % 13);
-      atomicAdd(&g->x, coef * (double)re);
-      atomicAdd(&g->y, coef * (double)im);
+  }
+}
+
+// G[I][t] = sum over the column sets of P[set][I][t], sets in fixed order
+__global__ void grad_reduce_kernel(int64_t n, int groups, const double2* __restrict__ P, double2* __restrict__ G) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 s = P[e];
+    for (int g = 1; g < groups; ++g) {
+      const double2 v = P[(int64_t)g * n + e];
+      s.x += v.x;
+      s.y += v.y;
     }
+    G[e] = s;
   }
 }
 
@@ -294,19 +404,42 @@ cudaError_t launch_seed_scatter(const ChebPlan& p, int prec, void* lam, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_accum(const ChebPlan& p, int prec, const void* lam, const void* alpha, double coef,
-                              double2* G, cudaStream_t s) {
-  const int N = p.nx * p.ny;
+int grad_groups(const ChebPlan& p, int prec) {
   if (prec == KPM_FP32) {
-    // a few column groups per site: enough CTAs for the GPU, few atomics per entry
-    const int64_t groups = (p.ldv / 2 + 31) / 32;
-    const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(groups, std::max<int64_t>(1, 8 * 152 * 8 / std::max(N, 1))));
-    const dim3 grid((N + 7) / 8, (unsigned)gy);
-    grad_accum_f32_kernel<<<grid, 256, 0, s>>>(p.nx, p.ny, p.ldv, (const float4*)lam, (const float4*)alpha, coef, G);
+    // one CTA per SM (158 KB of stages): about two waves of (tile, set) CTAs
+    const int64_t tiles = (int64_t)((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY);
+    const int64_t nblk = (p.ldv / 2 + kQ - 1) / kQ;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((2 * kSMs) / tiles, nblk), 64));
+  }
+  // about two waves of 24 row-warps per SM, at least one 32-column stride per set
+  const int64_t want = (2 * kSMs * 24 + p.D - 1) / std::max<int64_t>(p.D, 1);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, (p.ldv + 31) / 32), 16));
+}
+
+cudaError_t launch_grad_accum(const ChebPlan& p, int prec, const void* lam, const void* alpha, double coef,
+                              double2* P, cudaStream_t s) {
+  const int groups = grad_groups(p, prec);
+  if (prec == KPM_FP32) {
+    // per-function attribute of the current device (cheap host call)
+    cudaError_t e = cudaFuncSetAttribute(grad_tile_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTileSmem);
+    if (e != cudaSuccess) return e;
+    const int tiles_x = (p.nx + kTX - 1) / kTX;
+    const dim3 grid((unsigned)(tiles_x * ((p.ny + kTY - 1) / kTY)), (unsigned)groups);
+    grad_tile_f32_kernel<<<grid, kTileThreads, kTileSmem, s>>>(p.nx, p.ny, p.ldv / 2, tiles_x, (const float4*)lam,
+                                                               (const float4*)alpha, coef, P);
     return cudaGetLastError();
   }
-  const dim3 grid((N + kGradSites - 1) / kGradSites, (unsigned)((p.ldv + kGradCols - 1) / kGradCols));
-  grad_accum_kernel<<<grid, kGradSites * kGradCols, 0, s>>>(p.nx, p.ny, p.ldv, prec, lam, alpha, coef, G);
+  const dim3 grid((unsigned)((p.D + kGradRows - 1) / kGradRows), (unsigned)groups);
+  grad_rows_f64_kernel<<<grid, kGradRows * 32, 0, s>>>(p.nx, p.ny, p.ldv, (const double2*)lam,
+                                                        (const double2*)alpha, coef, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(int64_t D, int groups, const double2* P, double2* G, cudaStream_t s) {
+  const int64_t n = D * 13;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * kSMs));
+  grad_reduce_kernel<<<grid, 256, 0, s>>>(n, groups, P, G);
   return cudaGetLastError();
 }
 

@@ -179,6 +179,14 @@ struct PassPlan {
   size_t elem;    // bytes per complex
 };
 
+// the widest equal split of D unit columns into slabs of at most `width`
+// columns (a ragged last slab would cost a full slab's launches)
+int64_t balanced_width(int64_t D, int64_t width) {
+  if (width >= D) return D;
+  const int64_t n = (D + width - 1) / width;
+  return (D + n - 1) / n;
+}
+
 int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp) {
   if (!o) return fail(ctx, KPM_EINVAL, "opts is null");
   if (o->M < 1) return fail(ctx, KPM_EINVAL, "M must be >= 1");
@@ -189,7 +197,7 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, D) : D;
   if (o->block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / (2 * (uint64_t)D * pp->elem));
-    width = std::min<int64_t>(width, std::max<int64_t>(fit, 1));
+    width = balanced_width(D, std::min<int64_t>(width, std::max<int64_t>(fit, 1)));
   }
   pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
   if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
@@ -600,7 +608,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const size_t elem = o.precision == KPM_FP32 ? 8 : 16;
   if (o.block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((uint64_t)(nvec + 2) * D * elem));
-    o.block_width = (int)std::max<int64_t>(1, std::min<int64_t>(D, fit));
+    o.block_width = (int)balanced_width(D, std::max<int64_t>(1, std::min<int64_t>(D, fit)));
   }
   PassPlan pp;
   if ((r = plan_pass(ctx, model, &o, &pp))) return r;
@@ -608,7 +616,10 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const ChebPlan& p = pp.cheb;
   const size_t vbytes = (size_t)D * p.ldv * elem;
   if ((r = ensure(ctx, &ctx->bwd, &ctx->bwd_bytes, vbytes * (size_t)nvec))) return r;
-  if ((r = ensure(ctx, &ctx->Gacc, &ctx->Gacc_bytes, (size_t)D * 13 * sizeof(double2)))) return r;
+  const int groups = grad_groups(p, o.precision);
+  const size_t gbytes = (size_t)D * 13 * sizeof(double2);  // G, then the column sets' partial sums
+  if ((r = ensure(ctx, &ctx->Gacc, &ctx->Gacc_bytes, gbytes * (size_t)(groups + 1)))) return r;
+  double2* Gpart = ctx->Gacc + (size_t)D * 13;
   if ((r = ensure(ctx, &ctx->wseed, &ctx->wseed_bytes, (size_t)D * kSlots * sizeof(double2)))) return r;
   char* base = static_cast<char*>(ctx->bwd);
   auto ckpt = [&](int k) { return (void*)(base + vbytes * (size_t)k); };
@@ -626,7 +637,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   else
     KPM_CU(launch_scale_table_f64(*model, fields, ab, (double2*)ctx->table, s));
   KPM_CU(launch_seed_weights(model->nx, model->ny, grad_obs, ab, grad_omega, ctx->wseed, s));
-  KPM_CU(cudaMemsetAsync(ctx->Gacc, 0, (size_t)D * 13 * sizeof(double2), s));
+  KPM_CU(cudaMemsetAsync(Gpart, 0, gbytes * (size_t)groups, s));
   const double* am = ctx->am;
   const double* ao = ctx->ao;
 
@@ -674,11 +685,12 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
         // lnxt <- 2 h~ lambda_{m+1} - lambda_{m+2} + c_m = lambda_m
         KPM_CU(launch_cheb_step(p, prec, ctx->table, lcur, lnxt, s0, nullptr, am, ao, 0, 1, s));
         KPM_CU(launch_seed_scatter(p, prec, lnxt, s0, ctx->wseed, am, ao, m, s));
-        KPM_CU(launch_grad_accum(p, prec, lnxt, segp[m - 1 - k * seg], m == 1 ? 1.0 : 2.0, ctx->Gacc, s));
+        KPM_CU(launch_grad_accum(p, prec, lnxt, segp[m - 1 - k * seg], m == 1 ? 1.0 : 2.0, Gpart, s));
         std::swap(lcur, lnxt);
       }
     }
   }
+  KPM_CU(launch_grad_reduce(D, groups, Gpart, ctx->Gacc, s));
   KPM_CU(launch_grad_fields(model->nx, model->ny, ctx->Gacc, ab, grad_fields, s));
   if (grad_phi) KPM_CU(launch_phi_grad(*model, phi, params, grad_fields, grad_phi, s));
   return KPM_OK;
@@ -967,8 +979,10 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   KPM_CU(cudaEventCreate(&e1));
   // candidates: full width and narrower slabs (down to L2-resident ones), every column chunk
   std::vector<int64_t> widths = {D};
-  for (int64_t w : {8192, 4096, 2048, 1024, 512, 384, 256, 128})
-    if (w < D) widths.push_back(w);
+  for (int64_t w : {8192, 4096, 2048, 1024, 512, 384, 256, 128}) {
+    const int64_t bw = balanced_width(D, w);
+    if (bw < widths.back()) widths.push_back(bw);
+  }
   std::vector<int> cols = prec == KPM_FP32 ? std::vector<int>{16, 8, 4} : std::vector<int>{8, 4, 2};
   const int Mt = 32;  // trial order: init/gather amortised, well under a second per trial at 10^4 sites
   double best_t = 1e300;

@@ -93,9 +93,13 @@ cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const do
 // lambda[K_s(J), c] += coef_s(m) w[J][s] over the slab's columns
 cudaError_t launch_seed_scatter(const ChebPlan& p, int prec, void* lam, int64_t s0, const double2* w,
                                 const double* am, const double* ao, int m, cudaStream_t s);
-// G[I][k] += coef sum_c lam[I, c] conj(alpha[K_k(I), c]) over the 13 stencil entries of each row
+// column sets of the stencil-entry sums (partial buffer P holds grad_groups x D x 13 entries)
+int grad_groups(const ChebPlan& p, int prec);
+// P[set][I][k] += coef sum_{c in set} lam[I, c] conj(alpha[K_k(I), c]) over the 13 stencil entries of each row
 cudaError_t launch_grad_accum(const ChebPlan& p, int prec, const void* lam, const void* alpha, double coef,
-                              double2* G, cudaStream_t s);
+                              double2* P, cudaStream_t s);
+// G[I][k] = sum over the sets of P[set][I][k] (fixed order)
+cudaError_t launch_grad_reduce(int64_t D, int groups, const double2* P, double2* G, cudaStream_t s);
 // dL/d(eps, T, D) from G (gradient in h~) with h~ = (h - b)/a
 cudaError_t launch_grad_fields(int nx, int ny, const double2* G, const double* ab, double* out, cudaStream_t s);
 // dL/dphi through the fields' dependence on the Peierls phases (rmft_kernels.cu)

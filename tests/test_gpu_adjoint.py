@@ -76,15 +76,17 @@ def test_backward_fp64_matches_oracle(K, nx, ny, M, bw, ckpt):
     assert np.max(np.abs(gphi - ref_phi)) < 1e-10 * max(1.0, np.max(np.abs(ref_phi)))
 
 
-def test_backward_fp32_matches_oracle(K):
+# lattices inside one 16 x 8 site tile, across ragged tiles in x and y, slabs
+# whose column-pair count is not a multiple of the 8-pair stage
+@pytest.mark.parametrize("nx,ny,M,bw,ckpt", [(12, 8, 128, 0, 12), (18, 10, 96, 40, 7), (33, 17, 64, 0, 0)])
+def test_backward_fp32_matches_oracle(K, nx, ny, M, bw, ckpt):
     kpm, _ = K
-    nx, ny, M = 12, 8, 128
     w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), M)
     p = inputs.vortex_seed(w)
     model, phi, params, fields, ab = _prep(K, nx, ny, p)
     rng = np.random.default_rng(5)
     g_obs, g_om = rng.normal(size=26 * nx * ny), 0.7
-    got, _ = _gpu_grad(K, model, fields, ab, M, kpm.KPM_FP32, g_obs, g_om, ckpt=12)
+    got, _ = _gpu_grad(K, model, fields, ab, M, kpm.KPM_FP32, g_obs, g_om, bw=bw, ckpt=ckpt)
     ref = adjoint.vjp_dense(rmft.Model(nx, ny), fields.cpu().numpy(), *ab.cpu().numpy(), M, g_obs, g_om)
     assert np.max(np.abs(got - ref)) < 2e-5 * max(1.0, np.max(np.abs(ref)))
 
@@ -186,3 +188,16 @@ def test_adjoint_64x64_checkpoints_every_32(K):
         v = rng.normal(size=26 * N)
         fd = (L(fields + h * dev(v)) - L(fields - h * dev(v))) / (2 * h)
         assert float(np.dot(got, v)) == pytest.approx(fd, rel=2e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_backward_is_deterministic(K, prec):
+    """The stencil-entry sums use no atomics: two calls agree bit for bit."""
+    kpm, ctx = K
+    nx, ny, M = 12, 10, 96
+    model, phi, params, fields, ab = _prep(K, nx, ny, inputs.random_params(nx, ny, 3))
+    g = np.random.default_rng(5).normal(size=26 * nx * ny)
+    p = kpm.KPM_FP32 if prec == "fp32" else kpm.KPM_FP64
+    a, _ = _gpu_grad(K, model, fields, ab, M, p, g, 0.7, bw=64, ckpt=7)
+    b, _ = _gpu_grad(K, model, fields, ab, M, p, g, 0.7, bw=64, ckpt=7)
+    assert np.array_equal(a, b)
