@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--double-step", action="store_true",
+                    help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
     ap.add_argument("--profile-small", action="store_true",
@@ -214,10 +216,10 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel_key, ldv):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; scaled to the benchmark's slab width."""
-    path = os.path.join(ROOT, "profiles", "cheb_step_fp32_100x100.json")
+def measured_traffic(name, kernel_key, ldv):
+    """DRAM bytes per launch from the committed ncu summary `name`, if it was
+    taken on the current kernel source; scaled to the benchmark's slab width."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
@@ -256,7 +258,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = kpm.kpm_create(local)
     model = kpm.make_model(w.nx, w.ny, w.t, w.tp, w.J, w.flux)
-    opts = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols)
+    opts = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols,
+                         flags=kpm.KPM_FLAG_DOUBLE_STEP if args.double_step else 0)
     ropts = kpm.make_rmft_opts(w.n_target, tol=0.0)
     phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
     kpm.kpm_peierls_phases(ctx, model, phi)
@@ -290,10 +293,11 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    rec_ms, rec_launches, launches, last = 0.0, 0, 0, None
+    rec_ms, rec_bytes, rec_launches, launches, last = 0.0, 0.0, 0, 0, None
     for _ in range(args.steps):
         _, st = kpm.rmft_iterate(ctx, model, opts, ropts, phi, params, mu, 1)
         rec_ms += st.recursion_ms
+        rec_bytes += st.recursion_bytes
         rec_launches += st.recursion_launches
         launches += st.kernel_launches
         last = st
@@ -339,18 +343,26 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel: the recursion step, timed live by the
-    # library's CUDA events around the step launches of every timed iteration
+    # roofline of the dominant kernel: the recursion, timed live by the
+    # library's CUDA events around the step launches of every timed iteration;
+    # algorithmic bytes = the slab vectors each launch must stream (double
+    # step: read V_{m-1}, V_m, write V_{m+1}, V_{m+2}; single step: read V_m,
+    # V_{m-1}, write V_{m+1}; 8 B per complex element), summed by the library
     cb = opts.cols_per_block if opts.cols_per_block > 0 else 16
     width = opts.block_width if 0 < opts.block_width < D else D
     ldv = (width + cb - 1) // cb * cb
     per_launch_s = rec_ms / 1e3 / max(rec_launches, 1)
-    alg_bytes = 24 * D * ldv  # read V_m, read V_{m-1}, write V_{m+1}: 3 x 8 B per complex element
+    alg_bytes = rec_bytes / max(rec_launches, 1)
+    vecs_per_launch = alg_bytes / (D * ldv * 8)
+    dbl = vecs_per_launch > 3.5
+    kname = "cheb_step2_f32_kernel" if dbl else "cheb_step_f32_kernel<16,1>"
     pk, pk_kind = peaks()
-    achieved = alg_bytes / per_launch_s / 1e9
+    achieved = rec_bytes / (rec_ms / 1e3) / 1e9
+    nslab = 4 if dbl else 2
     # the committed ncu counters were taken on a slab larger than L2; they
     # scale to full-width slabs only
-    traffic = measured_traffic(kernel_hash(), ldv) if width == D else None
+    traffic = measured_traffic("cheb_step2_fp32_100x100.json" if dbl else "cheb_step_fp32_100x100.json",
+                               kernel_hash(), ldv) if width == D else None
 
     fp64 = None
     if not args.no_fp64:
@@ -395,13 +407,14 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": w.nx, "ny": w.ny, "D": D, "M": M, "precision": "fp32 vectors, fp64 sums",
                    "slab_width": width, "cols_per_block": cb, "autotune": tune,
-                   "s_per_rmft_iteration": t / args.steps, "slab_bytes": 2 * D * ldv * 8,
-                   "l2": ("inputs larger than L2 (two recursion slabs of %.2f GB)" % (D * ldv * 8 / 1e9))
-                   if 2 * D * ldv * 8 > 129e6 else "recursion slabs L2-resident (%.0f MB)" % (2 * D * ldv * 8 / 1e6),
+                   "s_per_rmft_iteration": t / args.steps, "slab_bytes": nslab * D * ldv * 8,
+                   "recursion": "two steps per launch" if dbl else "one step per launch",
+                   "l2": ("inputs larger than L2 (%d recursion slabs of %.2f GB)" % (nslab, D * ldv * 8 / 1e9))
+                   if D * ldv * 8 > 129e6 else "recursion slabs L2-resident (%.0f MB)" % (nslab * D * ldv * 8 / 1e6),
                    "parallelism": f"{world} independent cells (one per GPU)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "cheb_step_f32_kernel<16,1>", "peak_kind": pk_kind,
+                     "kernel": kname, "peak_kind": pk_kind,
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": per_launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -75,7 +75,14 @@ typedef struct {
                            context's scratch budget (kpm_set_scratch_budget) */
   int32_t cols_per_block; /* columns per CTA in the recursion kernel; 0 = default */
   double margin;        /* spectral half-width margin of the Gershgorin rescale (0.01) */
+  int32_t flags;        /* KPM_FLAG_* bits; 0 = defaults */
+  int32_t reserved;     /* 0 */
 } kpm_opts;
+
+/* kpm_opts.flags: run the FP32 recursion two steps per launch where the
+ * lattice allows it (default: one step per launch; both give the same bits;
+ * kpm_autotune picks the faster) */
+#define KPM_FLAG_DOUBLE_STEP 1
 
 /* Self-consistency options (the paper's iteration, readings R1/R2). */
 typedef struct {
@@ -98,6 +105,9 @@ typedef struct {
   double recursion_ms;  /* device time of the Chebyshev recursion steps, summed over
                            this call's iterations (CUDA events recorded on the
                            launching stream around the step launches) */
+  double recursion_bytes; /* algorithmic HBM bytes of those launches, summed the same
+                           way: slab vectors each launch must read and write
+                           (8 B per FP32 / 16 B per FP64 complex element) */
   int32_t iterations;   /* iterations performed by this call */
   int32_t converged;    /* 1 if the last iteration met tol */
   int32_t kernel_launches;    /* kernels of this library launched per iteration */
@@ -159,9 +169,10 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
 
 /* Autotuner of the recursion launch: times a short pass (M = 32) for every
  * slab width in {D, 8192, ..., 128} (narrow slabs keep both recursion
- * vectors in L2) and every column chunk that fits shared memory, and writes
- * the fastest (block_width, cols_per_block) into *best (other fields copied
- * from *opts).  Results are cached per (nx, ny, precision) in the context
+ * vectors in L2), every column chunk that fits shared memory and (FP32) one
+ * or two steps per launch, and writes the fastest (block_width,
+ * cols_per_block, KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields
+ * copied from *opts).  Results are cached per (nx, ny, precision) in the context
  * (a cached answer returns *best_ms_per_step = -1).  fields, ab: device, as
  * for kpm_observables.  best_ms_per_step: host double or NULL. */
 int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,

@@ -69,7 +69,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -274,6 +273,96 @@ __device__ __forceinline__ void acc_term(Acc2& a, float2 c, ulonglong2 u) {
   a.qi = f2fma(ci, u.y, a.qi);
 }
 
+// 2h~ applied to site x of lattice row y for one column pair, both Nambu
+// rows: wm, w0, wp are lattice rows y-1, y, y+1 of a pair-split V in shared
+// memory ([nx][2][NV] float4, already offset by the thread's pair), cf_row the
+// row's 2h~ entries.  Returns the two output rows as (re pair, im pair).
+// SW: rows stored with the two Nambu halves of odd sites swapped (2-column-pair
+// chunks: keeps the 16-byte accesses of a warp's 8-lane phases on distinct banks)
+template <int NV, bool SW = false>
+__device__ __forceinline__ int nambu_slot(int x, int al) {
+  return SW ? (al ^ (x & 1)) : al;
+}
+
+template <int NV, bool SW = false>
+__device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0, const float4* wp,
+                                             const float2* cf_row, int x, int nx, ulonglong2& o0, ulonglong2& o1) {
+  constexpr int RS = 2 * NV;
+  const int xr = x + 1 == nx ? 0 : x + 1;
+  const int xl = x == 0 ? nx - 1 : x - 1;
+  const float2* cf = cf_row + x * kCoef;
+#define KPM_L(W, XX, AL) \
+  (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + nambu_slot<NV, SW>((XX), (AL)) * NV))
+  Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
+  {
+    const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
+    const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
+    const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+    a0.pr = f2fma(d0, u0.x, a0.pr);
+    a0.pi = f2fma(d0, u0.y, a0.pi);
+    a1.pr = f2fma(d1, u1.x, a1.pr);
+    a1.pi = f2fma(d1, u1.y, a1.pi);
+  }
+  // neighbours k = 1..8: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1)
+  const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
+  const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
+    const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
+    acc_term(a0, cf[1 + k], u0);
+    acc_term(a1, cf[9 + k], u1);
+    if (k < 4) {
+      acc_term(a0, cf[17 + k], u1);
+      acc_term(a1, cf[21 + k], u0);
+    }
+  }
+#undef KPM_L
+  o0 = make_ulonglong2(f2sub(a0.pr, a0.qi), f2add(a0.pi, a0.qr));
+  o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
+}
+
+// moment sums acc[J][s] += a V[K_s(J), J] for the columns of the chunk whose
+// own site lies in lattice row y; wm, w0, wp hold rows y-1, y, y+1
+template <int CB, bool SW = false>
+__device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, const float4* wp, int nx, int y,
+                                            int64_t D, int64_t s0, int64_t cb0, double cm, double co,
+                                            double2* __restrict__ acc) {
+  constexpr int NV = CB / 2;
+  constexpr int RS = 2 * NV;
+  for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
+    const int c = t / kSlots, s = t - c * kSlots;
+    const int64_t J = s0 + cb0 + c;
+    if (J >= D) continue;
+    const int64_t j = J >> 1;
+    if (j / nx != y) continue;
+    const int beta = (int)(J & 1);
+    const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
+    const int dy = kSlotDy[s];
+    const float4* w = dy < 0 ? wm : (dy > 0 ? wp : w0);
+    const int al = kSlotFlip[s] ? 1 - beta : beta;
+    const float2 val = pair_elem(w + xsl * RS + nambu_slot<NV, SW>(xsl, al) * NV, c);
+    const double coef_m = s == kSlots - 1 ? co : cm;
+    double2* a = acc + J * kSlots + s;
+    a->x += coef_m * (double)val.x;
+    a->y += coef_m * (double)val.y;
+  }
+}
+
+// one lattice row of a pair-split V into shared memory with the Nambu halves
+// of odd sites swapped (layout read through nambu_slot<NV, true>)
+template <int NV>
+__device__ __forceinline__ void stage_row_sw(float4* dst, const float4* __restrict__ V, int ly, int nx, int64_t ldq,
+                                             int64_t q0) {
+  const int total = 2 * nx * NV;
+  const float4* base = V + (int64_t)(2 * nx) * ly * ldq + q0;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int r = t / NV, c = t - r * NV;
+    const int x = r >> 1, al = r & 1;
+    cp_async16(dst + x * 2 * NV + (al ^ (x & 1)) * NV + c, base + (int64_t)r * ldq + c);
+  }
+}
+
 // FP32 step.  Shared memory: V_m window ring of 5 lattice rows (rows y-1..y+1
 // in use, y+2 and y+3 in flight) and a ring of 3 coefficient rows (y in use,
 // y+1 and y+2 in flight); V_{m-1} rows are read one row ahead into registers.
@@ -313,7 +402,8 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
     }
   }
 
-  // prologue groups: {V rows y0-1..y0+1, coef y0}, {V row y0+2, coef y0+1}, {V row y0+3, coef y0+2}
+  // prologue groups: {V rows y0-1..y0+1, coef y0}, {V row y0+2, coef y0+1};
+  // iteration q commits {V row y+3, coef y+2} right after its barrier
   for (int q = 0; q < 3; ++q)
     stage_row<float4, NV>(win + q * rowsz, Vcur, wrapi(y0 - 1 + q, ny), nx, ldq, q0);
   stage_coef<float2>(coef, table, y0, nx);
@@ -321,11 +411,6 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
   if (nrow >= 2) {
     stage_row<float4, NV>(win + 3 * rowsz, Vcur, wrapi(y0 + 2, ny), nx, ldq, q0);
     stage_coef<float2>(coef + crow, table, y0 + 1, nx);
-  }
-  cp_commit();
-  if (nrow >= 3) {
-    stage_row<float4, NV>(win + 4 * rowsz, Vcur, wrapi(y0 + 3, ny), nx, ldq, q0);
-    stage_coef<float2>(coef + 2 * crow, table, y0 + 2, nx);
   }
   cp_commit();
 
@@ -348,8 +433,17 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
   for (int q = 0; q < nrow; ++q) {
     const int y = y0 + q;
     if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, pn);
-    cp_wait_2();
+    cp_wait_1();
     __syncthreads();
+    // refill (every thread is past row y-1): V_m row y+3 into the slot of
+    // y-2, coefficients of y+2 into the slot of y-1
+    {
+      const int bf = bm == 0 ? 4 : bm - 1;
+      const int cfs = bc == 0 ? 2 : bc - 1;
+      if (y + 3 <= y1) stage_row<float4, NV>(win + bf * rowsz, Vcur, wrapi(y + 3, ny), nx, ldq, q0);
+      if (y + 2 < y1) stage_coef<float2>(coef + cfs * crow, table, y + 2, nx);
+      cp_commit();
+    }
     const int b0 = bm + 1 == 5 ? 0 : bm + 1;
     const int bp = b0 + 1 == 5 ? 0 : b0 + 1;
     const float4* wm = win + bm * rowsz + v;  // lattice row y - 1
@@ -361,36 +455,8 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
     for (int it = 0; it < 2; ++it) {
       if (!(it == 0 ? own0 : own1)) continue;
       const int x = xs + it * xstep;
-      const int xr = x + 1 == nx ? 0 : x + 1;
-      const int xl = x == 0 ? nx - 1 : x - 1;
-      const float2* cf = cf_row + x * kCoef;
-#define KPM_L(W, XX, AL) (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + (AL) * NV))
-      Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
-      {
-        const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
-        const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
-        const u64 d0 = dup2(d.x), d1 = dup2(d.y);
-        a0.pr = f2fma(d0, u0.x, a0.pr);
-        a0.pi = f2fma(d0, u0.y, a0.pi);
-        a1.pr = f2fma(d1, u1.x, a1.pr);
-        a1.pi = f2fma(d1, u1.y, a1.pi);
-      }
-      const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
-      const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
-        const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
-        acc_term(a0, cf[1 + k], u0);
-        acc_term(a1, cf[9 + k], u1);
-        if (k < 4) {
-          acc_term(a0, cf[17 + k], u1);
-          acc_term(a1, cf[21 + k], u0);
-        }
-      }
-#undef KPM_L
-      ulonglong2 o0 = make_ulonglong2(f2sub(a0.pr, a0.qi), f2add(a0.pi, a0.qr));
-      ulonglong2 o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
+      ulonglong2 o0, o1;
+      stencil_site<NV>(wm, w0, wp, cf_row, x, nx, o0, o1);
       if (MODE == 1) {
         o0.x = f2sub(o0.x, pc[it][0].x);
         o0.y = f2sub(o0.y, pc[it][0].y);
@@ -407,31 +473,8 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
       *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
     }
 
-    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi) {
-      const double cm = am[m], co = ao[m];
-      for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
-        const int c = t / kSlots, s = t - c * kSlots;
-        const int64_t J = s0 + cb0 + c;
-        if (J >= D) continue;
-        const int64_t j = J >> 1;
-        if (j / nx != y) continue;
-        const int beta = (int)(J & 1);
-        const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
-        const int dy = kSlotDy[s];
-        const float4* w = (dy < 0 ? wm : (dy > 0 ? wp : w0)) - v;
-        const int al = kSlotFlip[s] ? 1 - beta : beta;
-        const float2 val = pair_elem(w + xsl * RS + al * NV, c);
-        const double coef_m = s == kSlots - 1 ? co : cm;
-        double2* a = acc + J * kSlots + s;
-        a->x += coef_m * (double)val.x;
-        a->y += coef_m * (double)val.y;
-      }
-    }
-    __syncthreads();
-    // refill: V_m row y+4 into the slot of y-1, coefficients of y+3 into the slot of y
-    if (y + 4 <= y1) stage_row<float4, NV>(win + bm * rowsz, Vcur, wrapi(y + 4, ny), nx, ldq, q0);
-    if (y + 3 < y1) stage_coef<float2>(coef + bc * crow, table, y + 3, nx);
-    cp_commit();
+    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, s0, cb0, am[m], ao[m], acc);
     bm = b0;
     bc = bc + 1 == 3 ? 0 : bc + 1;
     if (MODE == 1) {
@@ -451,6 +494,177 @@ __global__ void __launch_bounds__(512, 1)
                          double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
                          int m) {
   f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, s0, acc, am, ao, m);
+}
+
+// FP32 double step: two recursion steps per launch (Eq. alpha applied twice),
+// from V_{m-1} (Vprev) and V_m (Vcur) to V_{m+1} (Vout1) and V_{m+2} (Vout2),
+// all four slabs distinct.  Per pair of steps the slabs are streamed once
+// (read V_{m-1}, V_m, write V_{m+1}, V_{m+2}: 4 x 8 B per row-column instead
+// of 6 x 8 B for two single steps).  The CTA marches a front f from y0-1 to
+// y1 over its band [y0, y1): at each f it computes V_{m+1}[f] from the V_m
+// window (rows f-1..f+1) into a 3-row shared ring, then V_{m+2}[f-1] from the
+// ring (rows f-2..f) and V_m[f-1]; the halo rows y0-1 and y1 of V_{m+1} are
+// computed by every band that needs them and not stored.  Moment sums: a_m V_m
+// at own row f, a_{m+1} V_{m+1} at own row f-1.  Shared memory: V_m ring of
+// 5 rows (3 in use, 2 in flight), V_{m+1} ring of 3 rows, coefficient ring of
+// 4 rows (f-1 and f in use, 2 in flight); two block barriers per front row.
+// Arithmetic is that of two single steps, so results agree bit for bit.
+template <int CB>
+__device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
+                                               const float2* __restrict__ table, const float4* __restrict__ Vprev,
+                                               const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
+                                               float4* __restrict__ Vout2, int64_t s0, double2* __restrict__ acc,
+                                               const double* __restrict__ am, const double* __restrict__ ao, int m) {
+  constexpr int NV = CB / 2;
+  constexpr int RS = 2 * NV;
+  constexpr bool SW = NV == 4;  // 8-column chunks: swap the Nambu halves of odd sites
+  const int64_t ldq = ldv / 2;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* win = reinterpret_cast<float4*>(smem_raw);              // [5][nx][2][NV]  V_m
+  float4* ring = win + 5 * nx * RS;                               // [3][nx][2][NV]  V_{m+1}
+  float2* coef = reinterpret_cast<float2*>(ring + 3 * nx * RS);   // [4][nx][kCoef]
+  const int rowsz = nx * RS;
+  const int crow = nx * kCoef;
+
+  const int64_t cb0 = (int64_t)blockIdx.y * CB;
+  const int64_t q0 = cb0 / 2;
+  const int y0 = blockIdx.x * ylen;
+  const int y1 = min(ny, y0 + ylen);
+  const int nrow = y1 - y0;
+
+  const int v = threadIdx.x % NV;
+  const int xs = threadIdx.x / NV;
+  const int xstep = blockDim.x / NV;
+  const bool own0 = xs < nx, own1 = xs + xstep < nx;
+
+  int yj_lo = ny, yj_hi = -1;
+  {
+    const int64_t Jlo = s0 + cb0, Jhi = min(D, s0 + cb0 + CB) - 1;
+    if (Jhi >= Jlo) {
+      yj_lo = (int)((Jlo >> 1) / nx);
+      yj_hi = (int)((Jhi >> 1) / nx);
+    }
+  }
+  auto stage_v = [&](float4* dst, int ly) {
+    if (SW)
+      stage_row_sw<NV>(dst, Vcur, ly, nx, ldq, q0);
+    else
+      stage_row<float4, NV>(dst, Vcur, ly, nx, ldq, q0);
+  };
+
+  // V_m row r lives in window slot (r - y0 + 2) % 5, its coefficients in slot
+  // (r - y0 + 2) % 4, V_{m+1} row r in ring slot (r - y0 + 1) % 3.  Prologue
+  // groups: {V rows y0-2..y0, coef y0-2, y0-1}, {V row y0+1, coef y0}; front
+  // step i commits {V row f+3, coef f+2} right after its first barrier.
+  for (int q = 0; q < 3; ++q) stage_v(win + q * rowsz, wrapi(y0 - 2 + q, ny));
+  stage_coef<float2>(coef, table, wrapi(y0 - 2, ny), nx);
+  stage_coef<float2>(coef + crow, table, wrapi(y0 - 1, ny), nx);
+  cp_commit();
+  stage_v(win + 3 * rowsz, wrapi(y0 + 1, ny));
+  stage_coef<float2>(coef + 2 * crow, table, y0, nx);
+  cp_commit();
+
+  ulonglong2 pc[2][2], pn[2][2];
+  const ulonglong2 zero2 = make_ulonglong2(0ull, 0ull);
+  auto load_prev = [&](int y, ulonglong2 (&dst)[2][2]) {
+    const float4* g = Vprev + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
+    const int64_t gstep = 2 * (int64_t)xstep * ldq;
+    dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
+    dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
+    dst[1][0] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep) : zero2;
+    dst[1][1] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep + ldq) : zero2;
+  };
+  load_prev(wrapi(y0 - 1, ny), pc);
+
+  const int nfront = nrow + 2;
+  for (int i = 0; i < nfront; ++i) {
+    const int f = y0 - 1 + i;          // front row (unwrapped)
+    const int fw = wrapi(f, ny);
+    if (i + 1 < nfront) load_prev(wrapi(f + 1, ny), pn);
+    cp_wait_1();
+    __syncthreads();
+    const int s5 = i % 5, s3 = i % 3, s4 = i % 4;
+    // refill the slots of V_m row f-2 and coefficient row f-2 (last read at front f-1)
+    {
+      const int w5 = s5 == 0 ? 4 : s5 - 1;
+      const int w4 = s4 == 0 ? 3 : s4 - 1;
+      if (f + 3 <= y1 + 1) stage_v(win + w5 * rowsz, wrapi(f + 3, ny));
+      if (f + 2 <= y1) stage_coef<float2>(coef + w4 * crow, table, wrapi(f + 2, ny), nx);
+      cp_commit();
+    }
+    const float4* wm = win + s5 * rowsz + v;                            // V_m row f-1
+    const float4* w0 = win + (s5 + 1 == 5 ? 0 : s5 + 1) * rowsz + v;     // f
+    const float4* wp = win + (s5 + 2 >= 5 ? s5 - 3 : s5 + 2) * rowsz + v;  // f+1
+    float4* rf = ring + s3 * rowsz + v;                                  // V_{m+1} row f
+
+    // phase A: V_{m+1}[f] = 2h~ V_m[f] - V_{m-1}[f]
+    {
+      const float2* cf_row = coef + (s4 + 1 == 4 ? 0 : s4 + 1) * crow;  // row f
+      const bool store = f >= y0 && f < y1;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        if (!(it == 0 ? own0 : own1)) continue;
+        const int x = xs + it * xstep;
+        ulonglong2 o0, o1;
+        stencil_site<NV, SW>(wm, w0, wp, cf_row, x, nx, o0, o1);
+        o0.x = f2sub(o0.x, pc[it][0].x);
+        o0.y = f2sub(o0.y, pc[it][0].y);
+        o1.x = f2sub(o1.x, pc[it][1].x);
+        o1.y = f2sub(o1.y, pc[it][1].y);
+        *reinterpret_cast<ulonglong2*>(rf + x * RS + nambu_slot<NV, SW>(x, 0) * NV) = o0;
+        *reinterpret_cast<ulonglong2*>(rf + x * RS + nambu_slot<NV, SW>(x, 1) * NV) = o1;
+        if (store) {
+          float4* g = Vout1 + (2 * ((int64_t)fw * nx + x)) * ldq + q0 + v;
+          *reinterpret_cast<ulonglong2*>(g) = o0;
+          *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
+        }
+      }
+      if (acc != nullptr && f >= y0 && f < y1 && f >= yj_lo && f <= yj_hi)
+        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, s0, cb0, am[m], ao[m], acc);
+    }
+    __syncthreads();
+
+    // phase B: V_{m+2}[f-1] = 2h~ V_{m+1}[f-1] - V_m[f-1]
+    if (i >= 2) {
+      const int g = f - 1;
+      const float4* rm = ring + (s3 + 1 == 3 ? 0 : s3 + 1) * rowsz + v;     // V_{m+1} row f-2
+      const float4* r0 = ring + (s3 + 2 >= 3 ? s3 - 1 : s3 + 2) * rowsz + v;  // f-1
+      const float2* cf_row = coef + s4 * crow;                             // row f-1
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        if (!(it == 0 ? own0 : own1)) continue;
+        const int x = xs + it * xstep;
+        ulonglong2 o0, o1;
+        stencil_site<NV, SW>(rm, r0, rf, cf_row, x, nx, o0, o1);
+        const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(wm + x * RS + nambu_slot<NV, SW>(x, 0) * NV);
+        const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(wm + x * RS + nambu_slot<NV, SW>(x, 1) * NV);
+        o0.x = f2sub(o0.x, b0.x);
+        o0.y = f2sub(o0.y, b0.y);
+        o1.x = f2sub(o1.x, b1.x);
+        o1.y = f2sub(o1.y, b1.y);
+        float4* gp = Vout2 + (2 * ((int64_t)g * nx + x)) * ldq + q0 + v;
+        *reinterpret_cast<ulonglong2*>(gp) = o0;
+        *reinterpret_cast<ulonglong2*>(gp + ldq) = o1;
+      }
+      if (acc != nullptr && g >= yj_lo && g <= yj_hi)
+        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, s0, cb0, am[m + 1], ao[m + 1], acc);
+    }
+    pc[0][0] = pn[0][0];
+    pc[0][1] = pn[0][1];
+    pc[1][0] = pn[1][0];
+    pc[1][1] = pn[1][1];
+  }
+  cp_wait_0();
+}
+
+template <int CB>
+__global__ void __launch_bounds__(512, 1)
+    cheb_step2_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
+                          const float4* __restrict__ Vprev, const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
+                          float4* __restrict__ Vout2, int64_t s0, double2* __restrict__ acc,
+                          const double* __restrict__ am, const double* __restrict__ ao, int m) {
+  f32_step2_body<CB>(nx, ny, D, ldv, ylen, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m);
 }
 
 // Batched step: cells of one shape, blockIdx.z selects the cell; every cell
@@ -544,6 +758,28 @@ template <int CB>
 size_t smem_f32(int nx) {  // V_m window ring of 5 rows + coefficient ring of 3 rows
   return sizeof(float4) * (size_t)5 * nx * CB + sizeof(float2) * (size_t)3 * nx * kCoef;
 }
+template <int CB>
+size_t smem_f32x2(int nx) {  // V_m ring of 5 rows + V_{m+1} ring of 3 rows + coefficient ring of 4 rows
+  return sizeof(float4) * (size_t)8 * nx * CB + sizeof(float2) * (size_t)4 * nx * kCoef;
+}
+size_t smem_f32x2_of(int cb, int nx) {
+  return cb == 16 ? smem_f32x2<16>(nx) : cb == 8 ? smem_f32x2<8>(nx) : cb == 4 ? smem_f32x2<4>(nx) : smem_f32x2<2>(nx);
+}
+template <int CB>
+cudaError_t set_smem_f32x2() {
+  return cudaFuncSetAttribute(cheb_step2_f32_kernel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+}
+template <int CB>
+cudaError_t launch_f32x2(const ChebPlan& p, const void* table, const void* Vprev, const void* Vcur, void* Vout1,
+                         void* Vout2, int64_t s0, double2* acc, const double* am, const double* ao, int m,
+                         cudaStream_t s) {
+  const dim3 grid((p.ny + p.ylen2 - 1) / p.ylen2, (unsigned)(p.ldv / CB));
+  cheb_step2_f32_kernel<CB><<<grid, p.nthreads, p.smem2, s>>>(
+      p.nx, p.ny, p.D, p.ldv, p.ylen2, (const float2*)table, (const float4*)Vprev, (const float4*)Vcur,
+      (float4*)Vout1, (float4*)Vout2, s0, acc, am, ao, m);
+  return cudaGetLastError();
+}
+
 template <int CB>
 size_t smem_f64(int nx) {  // V_m window + V_{m-1} rows + coefficient rows
   return sizeof(double2) * ((size_t)6 * 2 * nx * CB + (size_t)2 * nx * kCoef);
@@ -647,6 +883,9 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
       break;
     }
   }
+  p.cb2 = 0;
+  p.ylen2 = 0;
+  p.smem2 = 0;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the
@@ -655,12 +894,49 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   const int64_t want = 4 * kSMs;
   const int yblocks = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
   p.ylen = std::max(1, (ny + yblocks - 1) / yblocks);
+  if (precision == KPM_FP32) {
+    // double step: widest chunk (<= cb) whose three rings fit; bands of at
+    // least 4 rows (each band recomputes two halo rows of V_{m+1} and reads
+    // four halo rows of V_m), about two waves of one CTA per SM
+    for (int k = 0; k < 4; ++k) {
+      const int c2 = cands32[k];
+      if (c2 > p.cb || nx > 2 * (p.nthreads / (c2 / 2))) continue;
+      const size_t sm2 = smem_f32x2_of(c2, nx);
+      if (sm2 > kSmemLimit) continue;
+      const int64_t ch2 = p.ldv / c2;
+      const int yb2 = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (2 * kSMs + ch2 - 1) / ch2));
+      const int yl2 = (ny + yb2 - 1) / yb2;
+      if (yl2 >= 4) {
+        p.cb2 = c2;
+        p.ylen2 = yl2;
+        p.smem2 = sm2;
+        break;
+      }
+    }
+  }
   return p;
 }
 
 size_t table_bytes_per_site(int precision) { return (size_t)kCoef * (precision == KPM_FP32 ? 8 : 16); }
 
+cudaError_t launch_cheb_step2(const ChebPlan& p, const void* table, const void* Vprev, const void* Vcur,
+                              void* Vout1, void* Vout2, int64_t s0, double2* acc, const double* am,
+                              const double* ao, int m, cudaStream_t s) {
+  switch (p.cb2) {
+    case 16: return launch_f32x2<16>(p, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m, s);
+    case 8: return launch_f32x2<8>(p, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m, s);
+    case 4: return launch_f32x2<4>(p, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m, s);
+    case 2: return launch_f32x2<2>(p, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t cheb_prepare(const ChebPlan& p, int precision) {
+  if (precision == KPM_FP32 && p.cb2 > 0) {
+    cudaError_t e = p.cb2 == 16 ? set_smem_f32x2<16>() : p.cb2 == 8 ? set_smem_f32x2<8>()
+                  : p.cb2 == 4 ? set_smem_f32x2<4>() : set_smem_f32x2<2>();
+    if (e != cudaSuccess) return e;
+  }
   if (precision == KPM_FP32) {
     switch (p.cb) {
       case 16: return set_smem_f32<16>(p.nx);

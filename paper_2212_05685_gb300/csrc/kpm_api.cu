@@ -25,7 +25,8 @@ struct kpm_ctx {
   uint64_t budget = 24ull << 30;
 
   // scratch (owned)
-  void* slab[2] = {nullptr, nullptr};
+  void* slab[4] = {nullptr, nullptr, nullptr, nullptr};  // two, or four for the double-step recursion
+  int slab_n = 0;
   size_t slab_bytes = 0;
   double2* acc = nullptr;
   size_t acc_bytes = 0;
@@ -55,6 +56,7 @@ struct kpm_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int launches = 0;      // kernels per captured iteration
   int rec_launches = 0;  // recursion-step kernels per captured iteration
+  double rec_bytes = 0;  // their algorithmic bytes
 
   // batched iteration: per-cell scratch, fork streams, cached graph
   struct Cell {
@@ -75,8 +77,8 @@ struct kpm_ctx {
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
 
-  // autotuned (block_width, cols_per_block) per (nx, ny, precision)
-  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+  // autotuned (block_width, cols_per_block, flags) per (nx, ny, precision)
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -177,6 +179,7 @@ struct PassPlan {
   ChebPlan cheb;
   int64_t width;  // unit columns per slab
   size_t elem;    // bytes per complex
+  bool dbl;       // FP32 double-step recursion (four slabs)
 };
 
 // the widest equal split of D unit columns into slabs of at most `width`
@@ -194,36 +197,41 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
+  const bool want_dbl = o->precision == KPM_FP32 && (o->flags & KPM_FLAG_DOUBLE_STEP);
   int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, D) : D;
   if (o->block_width == 0) {
-    const int64_t fit = (int64_t)(ctx->budget / (2 * (uint64_t)D * pp->elem));
+    const int64_t fit = (int64_t)(ctx->budget / ((want_dbl ? 4 : 2) * (uint64_t)D * pp->elem));
     width = balanced_width(D, std::min<int64_t>(width, std::max<int64_t>(fit, 1)));
   }
   pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
   if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
   // slabs advance by the padded width: every unit column belongs to exactly one slab
   pp->width = pp->cheb.ldv;
+  pp->dbl = want_dbl && pp->cheb.cb2 > 0;
   return KPM_OK;
 }
 
 int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp) {
   const int64_t D = pp.cheb.D;
   const size_t slab = (size_t)D * pp.cheb.ldv * pp.elem;
+  const int nslab = pp.dbl ? 4 : 2;
   int r;
-  if (ctx->slab_bytes < slab) {
+  if (ctx->slab_bytes < slab || ctx->slab_n < nslab) {
     drop_graph(ctx);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
       if (ctx->slab[k]) cudaFree(ctx->slab[k]);
       ctx->slab[k] = nullptr;
     }
     ctx->slab_bytes = 0;
-    for (int k = 0; k < 2; ++k) {
+    ctx->slab_n = 0;
+    for (int k = 0; k < nslab; ++k) {
       if (cudaMalloc(&ctx->slab[k], slab) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, KPM_ENOMEM, "cudaMalloc of the recursion slabs failed");
       }
     }
     ctx->slab_bytes = slab;
+    ctx->slab_n = nslab;
   }
   const size_t accb = (size_t)D * kSlots * sizeof(double2);
   if (ctx->acc_bytes < accb) drop_graph(ctx);
@@ -261,37 +269,53 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
 // the last slab); *launches / *rec_launches count the kernels enqueued.
 int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
                  const double* ab, double* obs, double* omega, cudaStream_t s, bool events = false,
-                 int* launches = nullptr, int* rec_launches = nullptr) {
+                 int* launches = nullptr, int* rec_launches = nullptr, double* rec_bytes = nullptr) {
   const ChebPlan& p = pp.cheb;
   const int M = o->M;
   const int prec = o->precision;
   int nl = 0, nr = 0;
+  double nb = 0.0;
+  const double vec = (double)p.D * (double)p.ldv * (double)pp.elem;  // bytes of one slab vector
   KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
   else
     KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
   nl += 2;
-  void* A = ctx->slab[0];
-  void* B = ctx->slab[1];
   for (int64_t s0 = 0; s0 < p.D; s0 += pp.width) {
-    KPM_CU(launch_cheb_init(p, prec, A, s0, ctx->acc, ctx->am, ctx->ao, s));
+    // X0 = V_{mm-1}, X1 = V_mm; Y0, Y1 the free pair of the double-step recursion
+    void* X0 = ctx->slab[0];
+    void* X1 = ctx->slab[1];
+    void* Y0 = pp.dbl ? ctx->slab[2] : nullptr;
+    void* Y1 = pp.dbl ? ctx->slab[3] : nullptr;
+    KPM_CU(launch_cheb_init(p, prec, X0, s0, ctx->acc, ctx->am, ctx->ao, s));
     nl += 1;
     if (events && s0 == 0) KPM_CU(cudaEventRecordWithFlags(ctx->ev[0], s, cudaEventRecordExternal));
     if (M >= 2) {
-      KPM_CU(launch_cheb_step(p, prec, ctx->table, A, B, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, X0, X1, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
       nr += 1;
+      nb += 2 * vec;
     }
-    for (int mm = 1; mm <= M - 2; ++mm) {
-      const void* cur = (mm & 1) ? B : A;
-      void* out = (mm & 1) ? A : B;
-      KPM_CU(launch_cheb_step(p, prec, ctx->table, cur, out, s0, ctx->acc, ctx->am, ctx->ao, mm, 1, s));
+    int mm = 1;  // highest vector index computed so far
+    if (pp.dbl) {
+      for (; mm + 2 <= M - 1; mm += 2) {
+        KPM_CU(launch_cheb_step2(p, ctx->table, X0, X1, Y0, Y1, s0, ctx->acc, ctx->am, ctx->ao, mm, s));
+        nr += 1;
+        nb += 4 * vec;
+        std::swap(X0, Y0);
+        std::swap(X1, Y1);
+      }
+    }
+    for (; mm + 1 <= M - 1; ++mm) {
+      // V_{mm+1} = 2 h~ V_mm - V_{mm-1} in place over V_{mm-1}
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, X1, X0, s0, ctx->acc, ctx->am, ctx->ao, mm, 1, s));
       nr += 1;
+      nb += 3 * vec;
+      std::swap(X0, X1);
     }
     if (events && s0 + pp.width >= p.D) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
     if (M >= 2) {
-      const void* last = ((M - 1) & 1) ? B : A;
-      KPM_CU(launch_cheb_gather(p, prec, last, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
+      KPM_CU(launch_cheb_gather(p, prec, X1, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
       nl += 1;
     }
   }
@@ -299,6 +323,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   nl += omega ? 2 : 1;
   if (launches) *launches = nl + nr;
   if (rec_launches) *rec_launches = nr;
+  if (rec_bytes) *rec_bytes = nb;
   return KPM_OK;
 }
 
@@ -377,7 +402,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   drop_graph(ctx);
-  for (void* p : {ctx->slab[0], ctx->slab[1], (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
+  for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
     if (p) cudaFree(p);
@@ -515,11 +540,14 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     if (e == cudaSuccess) e = launch_shift_eps(N, ctx->fields, dmu, ctx->misc + 6, ctx->misc + 2, ctx->red, c);
     if (e == cudaSuccess) e = launch_gershgorin(*model, ctx->fields, opts->margin, ab, ctx->red, c);
     int npass = 0, nrec = 0;
+    double nbytes = 0.0;
     if (e == cudaSuccess)
-      rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c, true, &npass, &nrec);
+      rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c, true, &npass, &nrec,
+                        &nbytes);
     // fields 1, mean-shift 3, bounds 2, pass, update 4
     ctx->launches = 1 + 3 + 2 + npass + 4;
     ctx->rec_launches = nrec;
+    ctx->rec_bytes = nbytes;
     if (e == cudaSuccess && rr == KPM_OK)
       e = launch_update(N, dpar, ctx->obs, dmu, *ropts, ctx->misc + 4, ctx->red, c);
     if (e == cudaSuccess && rr == KPM_OK)
@@ -557,6 +585,7 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
       float ms = 0.f;
       KPM_CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
       st.recursion_ms += ms;
+      st.recursion_bytes += ctx->rec_bytes;
     }
     const double* h = ctx->host_misc;
     st.a = h[0];
@@ -603,8 +632,10 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int K = M >= 2 ? (M - 1 + seg - 1) / seg : 0;  // segments, each serving m in [k seg + 1, (k+1) seg]
   const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
 
-  // slab width from the budget over all adjoint slab vectors (plus the forward pair)
+  // slab width from the budget over all adjoint slab vectors (plus the forward pair);
+  // the adjoint steps one moment per launch (its recomputed segments are stored)
   kpm_opts o = *opts;
+  o.flags &= ~KPM_FLAG_DOUBLE_STEP;
   const size_t elem = o.precision == KPM_FP32 ? 8 : 16;
   if (o.block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((uint64_t)(nvec + 2) * D * elem));
@@ -967,8 +998,9 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   auto key = std::make_tuple(model->nx, model->ny, prec);
   auto hit = ctx->tuned.find(key);
   if (hit != ctx->tuned.end()) {
-    best->block_width = hit->second.first;
-    best->cols_per_block = hit->second.second;
+    best->block_width = std::get<0>(hit->second);
+    best->cols_per_block = std::get<1>(hit->second);
+    best->flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | std::get<2>(hit->second);
     if (best_ms_per_step) *best_ms_per_step = -1.0;
     return KPM_OK;
   }
@@ -986,16 +1018,19 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   std::vector<int> cols = prec == KPM_FP32 ? std::vector<int>{16, 8, 4} : std::vector<int>{8, 4, 2};
   const int Mt = 32;  // trial order: init/gather amortised, well under a second per trial at 10^4 sites
   double best_t = 1e300;
-  int best_w = 0, best_c = 0;
+  int best_w = 0, best_c = 0, best_f = 0;
+  std::vector<int> modes = prec == KPM_FP32 ? std::vector<int>{0, KPM_FLAG_DOUBLE_STEP} : std::vector<int>{0};
   for (int64_t w : widths) {
-    for (int c : cols) {
+    for (int c : cols) for (int mode : modes) {
       kpm_opts o = *opts;
       o.M = Mt;
       o.block_width = (int)std::min<int64_t>(w, D);
       o.cols_per_block = c;
+      o.flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | mode;
       PassPlan pp;
       if (plan_pass(ctx, model, &o, &pp) != KPM_OK) continue;
       if (pp.cheb.cb != c) continue;  // chunk does not fit for this lattice
+      if (mode && !pp.dbl) continue;  // no double-step plan for this lattice
       if ((r = ensure_pass_scratch(ctx, model, &o, pp))) break;
       // one warm-up pass, one timed
       if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
@@ -1010,6 +1045,7 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
         best_t = per_step;
         best_w = o.block_width;
         best_c = c;
+        best_f = mode;
       }
     }
     if (r) break;
@@ -1018,9 +1054,10 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   cudaEventDestroy(e1);
   if (r) return r;
   if (best_c == 0) return fail(ctx, KPM_EINVAL, "no recursion configuration fits this lattice");
-  ctx->tuned[key] = std::make_pair(best_w, best_c);
+  ctx->tuned[key] = std::make_tuple(best_w, best_c, best_f);
   best->block_width = best_w;
   best->cols_per_block = best_c;
+  best->flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | best_f;
   if (best_ms_per_step) *best_ms_per_step = best_t;
   return KPM_OK;
 }

@@ -23,6 +23,10 @@ struct ChebPlan {
   int ylen;        // lattice rows marched per CTA
   int nthreads;
   size_t smem;     // dynamic shared memory per CTA
+  // FP32 double-step kernel (two recursion steps per launch); cb2 = 0: not used
+  int cb2;         // columns per CTA (divides cb)
+  int ylen2;       // lattice rows per band
+  size_t smem2;
 };
 
 // Per-cell pointers of a batch of equally shaped cells (FP32 recursion).
@@ -77,6 +81,11 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
 cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table, const void* Vcur,
                              void* Vout, int64_t s0, double2* acc, const double* am,
                              const double* ao, int m, int mode, cudaStream_t s, const void* Vprev = nullptr);
+// FP32 double step: Vout1 = V_{m+1}, Vout2 = V_{m+2} from Vprev = V_{m-1}, Vcur = V_m
+// (four distinct slabs), accumulating a_m V_m and a_{m+1} V_{m+1} unless acc is null
+cudaError_t launch_cheb_step2(const ChebPlan& p, const void* table, const void* Vprev, const void* Vcur,
+                              void* Vout1, void* Vout2, int64_t s0, double2* acc, const double* am,
+                              const double* ao, int m, cudaStream_t s);
 // batched FP32 step over ncell cells of one shape (plan p, full-width slabs)
 cudaError_t cheb_prepare_batched(const ChebPlan& p);
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,

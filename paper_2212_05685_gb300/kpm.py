@@ -23,6 +23,7 @@ KPM_ETIMEDOUT = -5
 KPM_ENOTCONV = -6
 KPM_FP64 = 0
 KPM_FP32 = 1
+KPM_FLAG_DOUBLE_STEP = 1
 
 
 class kpm_model(ctypes.Structure):
@@ -33,7 +34,8 @@ class kpm_model(ctypes.Structure):
 
 class kpm_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("precision", ctypes.c_int32), ("block_width", ctypes.c_int32),
-                ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double)]
+                ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class kpm_rmft_opts(ctypes.Structure):
@@ -45,7 +47,8 @@ class kpm_rmft_opts(ctypes.Structure):
 class kpm_rmft_stats(ctypes.Structure):
     _fields_ = [("residual", ctypes.c_double), ("density_error", ctypes.c_double), ("mu", ctypes.c_double),
                 ("omega", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
-                ("recursion_ms", ctypes.c_double), ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("recursion_ms", ctypes.c_double), ("recursion_bytes", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("recursion_launches", ctypes.c_int32)]
 
 
@@ -128,8 +131,8 @@ def make_model(nx, ny, t=1.0, tp=-0.3, J=0.3, flux=1, gutzwiller=True):
     return kpm_model(nx, ny, flux, 1 if gutzwiller else 0, t, tp, J)
 
 
-def make_opts(M, precision=KPM_FP32, block_width=0, cols_per_block=0, margin=0.01):
-    return kpm_opts(M, precision, block_width, cols_per_block, margin)
+def make_opts(M, precision=KPM_FP32, block_width=0, cols_per_block=0, margin=0.01, flags=0):
+    return kpm_opts(M, precision, block_width, cols_per_block, margin, flags, 0)
 
 
 def make_rmft_opts(n_target, alpha=0.5, alpha_n=0.05, eta=0.5, tol=1e-7, paramagnetic=True):

@@ -57,9 +57,30 @@ def test_strerror_and_refusals_without_gpu(lib):
     assert k.kpm_destroy(None) == kpm.KPM_EINVAL
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Field offsets and sizes of the ctypes structures equal those the C
+    compiler gives the header's structures."""
+    import shutil
+    import subprocess
     from paper_2212_05685_gb300 import kpm
-    assert ctypes.sizeof(kpm.kpm_model) == 40
-    assert ctypes.sizeof(kpm.kpm_opts) == 24
-    assert ctypes.sizeof(kpm.kpm_rmft_opts) == 48
-    assert ctypes.sizeof(kpm.kpm_rmft_stats) == 72
+    structs = [kpm.kpm_model, kpm.kpm_opts, kpm.kpm_rmft_opts, kpm.kpm_rmft_stats]
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kpm.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, (n, f)
