@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ph-half", action="store_true", help="skip the particle-hole half-pass section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
@@ -387,6 +388,41 @@ def run_ours(args):
                 "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
                 "fp32_speedup": t64 / (t / args.steps)}
 
+    # particle-hole half pass on the same cell (paramagnetic singlet sector:
+    # n_up = n_dn, chi_up = chi_dn, F_ij = F_ji hold for the seed and are kept)
+    ph_half = None
+    if not args.no_ph_half:
+        oh = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols, flags=kpm.KPM_FLAG_PH_HALF)
+        if not args.no_autotune and args.block_width == 0 and args.cols == 0:
+            f0 = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+            ab0 = torch.empty(2, dtype=torch.float64, device="cuda")
+            kpm.kpm_build_H(ctx, model, phi, params, 0.0, f0)
+            kpm.kpm_bounds(ctx, model, f0, 0.01, ab0)
+            ab0[1] = 0.0
+            oh, _ = kpm.kpm_autotune(ctx, model, oh, f0, ab0)
+            del f0, ab0
+        ph = torch.tensor(p0, device="cuda")
+        mh = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            kpm.rmft_iterate(ctx, model, oh, ropts, phi, ph, mh, 1)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        hb, hm = 0.0, 0.0
+        for _ in range(args.steps):
+            _, sh = kpm.rmft_iterate(ctx, model, oh, ropts, phi, ph, mh, 1)
+            hb += sh.recursion_bytes
+            hm += sh.recursion_ms
+        h1.record(stream)
+        torch.cuda.synchronize()
+        th = h0.elapsed_time(h1) / 1e3 / args.steps
+        ph_half = {"s_per_rmft_iteration": th, "vector_moments_per_s": N * M / th,
+                   "speedup_vs_full_pass": (t / args.steps) / th,
+                   "recursion_achieved_gbs": hb / (hm / 1e3) / 1e9,
+                   "columns": f"{N} of {D} unit columns (j, up); the (j, dn) observables from the particle-hole relation",
+                   "flags": oh.flags, "block_width": oh.block_width, "cols_per_block": oh.cols_per_block}
+
     batched = None if args.no_batched else batched_section(kpm, inputs, torch)
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
     precision = precision_section(kpm, inputs, torch)
@@ -422,6 +458,7 @@ def run_ours(args):
         "clocks": clk,
         "fp64": fp64,
         "fp32_error": precision,
+        "ph_half": ph_half,
         "batched": batched,
         "adjoint": adjoint,
         "residual_last": last.residual if last else None,

@@ -83,6 +83,16 @@ typedef struct {
  * lattice allows it (default: one step per launch; both give the same bits;
  * kpm_autotune picks the faster) */
 #define KPM_FLAG_DOUBLE_STEP 1
+/* kpm_opts.flags: particle-hole half pass.  Only the N unit columns (j, up)
+ * are propagated; the spin-down observables and the other half of the grand
+ * potential's diagonal follow exactly from F_M(h~) = 1 - U conj(F_M(h~)) U^T,
+ * which holds when eps_up = eps_dn, T_up = T_dn and D_ij = D_ji (the
+ * paramagnetic singlet sector, where the spectrum is symmetric and b = 0).
+ * kpm_observables and rmft_iterate check the fields (deviation <= 1e-12 of the
+ * largest field) and that |b| <= 1e-12 a, else KPM_EINVAL; rmft_iterate
+ * rescales with b = 0 exactly.  Not accepted by kpm_backward,
+ * rmft_iterate_batched and kpm_observables_noalloc (KPM_EINVAL). */
+#define KPM_FLAG_PH_HALF 2
 
 /* Self-consistency options (the paper's iteration, readings R1/R2). */
 typedef struct {
@@ -172,7 +182,8 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
  * vectors in L2), every column chunk that fits shared memory and (FP32) one
  * or two steps per launch, and writes the fastest (block_width,
  * cols_per_block, KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields
- * copied from *opts).  Results are cached per (nx, ny, precision) in the context
+ * copied from *opts).  Results are cached per (nx, ny, precision,
+ * KPM_FLAG_PH_HALF) in the context
  * (a cached answer returns *best_ms_per_step = -1).  fields, ab: device, as
  * for kpm_observables.  best_ms_per_step: host double or NULL. */
 int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,

@@ -6,6 +6,8 @@
 // with the moment sums acc[J][s] += a_m V_m[K_s(J), J] over the nine local
 // rows K_s(J) of every column (and the grand-potential series on the diagonal)
 // fused into the step that reads V_m (Eqs. rho_KPM, F_KPM with unit r).
+// Slab column c holds the unit vector of row J = (s0 + c) << js: js = 0 all
+// D columns, js = 1 only the columns (j, up) of the particle-hole half pass.
 //
 // Layout: V is row-major, V[K][c] with K = 2 i + alpha the Nambu row and c the
 // column inside the slab; the row stride ldv is the slab width rounded up to
@@ -103,7 +105,7 @@ template <typename Real, int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const typename CT<Real>::C* __restrict__ table,
                      const typename CT<Real>::C* __restrict__ Vcur, const typename CT<Real>::C* Vprev,
-                     typename CT<Real>::C* Vout, int64_t s0, double2* __restrict__ acc,
+                     typename CT<Real>::C* Vout, int64_t s0, int js, double2* __restrict__ acc,
                      const double* __restrict__ am, const double* __restrict__ ao, int m) {
   using C = typename CT<Real>::C;
   using V = typename CT<Real>::V;
@@ -196,8 +198,9 @@ __global__ void __launch_bounds__(512, 1)
       const double cm = am[m], co = ao[m];
       for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
         const int c = t / kSlots, s = t - c * kSlots;
-        const int64_t J = s0 + cb0 + c;
-        if (J >= D) continue;
+        const int64_t col = s0 + cb0 + c;
+        if (col >= (D >> js)) continue;
+        const int64_t J = col << js;
         const int64_t j = J >> 1;
         if (j / nx != y) continue;
         const int beta = (int)(J & 1);
@@ -326,14 +329,15 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
 // own site lies in lattice row y; wm, w0, wp hold rows y-1, y, y+1
 template <int CB, bool SW = false>
 __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, const float4* wp, int nx, int y,
-                                            int64_t D, int64_t s0, int64_t cb0, double cm, double co,
+                                            int64_t D, int64_t s0, int js, int64_t cb0, double cm, double co,
                                             double2* __restrict__ acc) {
   constexpr int NV = CB / 2;
   constexpr int RS = 2 * NV;
   for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
     const int c = t / kSlots, s = t - c * kSlots;
-    const int64_t J = s0 + cb0 + c;
-    if (J >= D) continue;
+    const int64_t col = s0 + cb0 + c;
+    if (col >= (D >> js)) continue;
+    const int64_t J = col << js;
     const int64_t j = J >> 1;
     if (j / nx != y) continue;
     const int beta = (int)(J & 1);
@@ -369,7 +373,8 @@ __device__ __forceinline__ void stage_row_sw(float4* dst, const float4* __restri
 template <int CB, int MODE>
 __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
                                               const float2* __restrict__ table, const float4* __restrict__ Vcur,
-                                              const float4* Vprev, float4* Vout, int64_t s0, double2* __restrict__ acc,
+                                              const float4* Vprev, float4* Vout, int64_t s0, int js,
+                                              double2* __restrict__ acc,
                                               const double* __restrict__ am, const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;   // float4 (column pairs) per Nambu row of the chunk
   constexpr int RS = 2 * NV;   // float4 per site of a window row (both Nambu rows)
@@ -395,10 +400,10 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
   // rows of the chunk's own sites: only there are moment sums due
   int yj_lo = ny, yj_hi = -1;
   {
-    const int64_t Jlo = s0 + cb0, Jhi = min(D, s0 + cb0 + CB) - 1;
-    if (Jhi >= Jlo) {
-      yj_lo = (int)((Jlo >> 1) / nx);
-      yj_hi = (int)((Jhi >> 1) / nx);
+    const int64_t clo = s0 + cb0, chi = min(D >> js, s0 + cb0 + CB) - 1;
+    if (chi >= clo) {
+      yj_lo = (int)(((clo << js) >> 1) / nx);
+      yj_hi = (int)(((chi << js) >> 1) / nx);
     }
   }
 
@@ -474,7 +479,7 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
     }
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
-      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, s0, cb0, am[m], ao[m], acc);
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, s0, js, cb0, am[m], ao[m], acc);
     bm = b0;
     bc = bc + 1 == 3 ? 0 : bc + 1;
     if (MODE == 1) {
@@ -490,10 +495,10 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
 template <int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
-                         const float4* __restrict__ Vcur, const float4* Vprev, float4* Vout, int64_t s0,
+                         const float4* __restrict__ Vcur, const float4* Vprev, float4* Vout, int64_t s0, int js,
                          double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
                          int m) {
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, s0, acc, am, ao, m);
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, s0, js, acc, am, ao, m);
 }
 
 // FP32 double step: two recursion steps per launch (Eq. alpha applied twice),
@@ -513,8 +518,9 @@ template <int CB>
 __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
                                                const float2* __restrict__ table, const float4* __restrict__ Vprev,
                                                const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
-                                               float4* __restrict__ Vout2, int64_t s0, double2* __restrict__ acc,
-                                               const double* __restrict__ am, const double* __restrict__ ao, int m) {
+                                               float4* __restrict__ Vout2, int64_t s0, int js,
+                                               double2* __restrict__ acc, const double* __restrict__ am,
+                                               const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;
   constexpr int RS = 2 * NV;
   constexpr bool SW = NV == 4;  // 8-column chunks: swap the Nambu halves of odd sites
@@ -540,10 +546,10 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
 
   int yj_lo = ny, yj_hi = -1;
   {
-    const int64_t Jlo = s0 + cb0, Jhi = min(D, s0 + cb0 + CB) - 1;
-    if (Jhi >= Jlo) {
-      yj_lo = (int)((Jlo >> 1) / nx);
-      yj_hi = (int)((Jhi >> 1) / nx);
+    const int64_t clo = s0 + cb0, chi = min(D >> js, s0 + cb0 + CB) - 1;
+    if (chi >= clo) {
+      yj_lo = (int)(((clo << js) >> 1) / nx);
+      yj_hi = (int)(((chi << js) >> 1) / nx);
     }
   }
   auto stage_v = [&](float4* dst, int ly) {
@@ -621,7 +627,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         }
       }
       if (acc != nullptr && f >= y0 && f < y1 && f >= yj_lo && f <= yj_hi)
-        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, s0, cb0, am[m], ao[m], acc);
+        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, s0, js, cb0, am[m], ao[m], acc);
     }
     __syncthreads();
 
@@ -648,7 +654,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         *reinterpret_cast<ulonglong2*>(gp + ldq) = o1;
       }
       if (acc != nullptr && g >= yj_lo && g <= yj_hi)
-        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, s0, cb0, am[m + 1], ao[m + 1], acc);
+        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, s0, js, cb0, am[m + 1], ao[m + 1], acc);
     }
     pc[0][0] = pn[0][0];
     pc[0][1] = pn[0][1];
@@ -662,9 +668,9 @@ template <int CB>
 __global__ void __launch_bounds__(512, 1)
     cheb_step2_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
                           const float4* __restrict__ Vprev, const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
-                          float4* __restrict__ Vout2, int64_t s0, double2* __restrict__ acc,
+                          float4* __restrict__ Vout2, int64_t s0, int js, double2* __restrict__ acc,
                           const double* __restrict__ am, const double* __restrict__ ao, int m) {
-  f32_step2_body<CB>(nx, ny, D, ldv, ylen, table, Vprev, Vcur, Vout1, Vout2, s0, acc, am, ao, m);
+  f32_step2_body<CB>(nx, ny, D, ldv, ylen, table, Vprev, Vcur, Vout1, Vout2, s0, js, acc, am, ao, m);
 }
 
 // Batched step: cells of one shape, blockIdx.z selects the cell; every cell
@@ -679,37 +685,38 @@ __global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, i
     cur = reinterpret_cast<const float4*>(b.A[z]);
     out = reinterpret_cast<float4*>(b.B[z]);
   }
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out, 0,
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out, 0, 0,
                           b.acc[z], b.am[z], b.ao[z], m);
 }
 
-// V0 = unit vectors e_{s0 + c} (zero elsewhere) and the m = 0 moment terms
-__global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, double2* __restrict__ V0, int64_t s0,
-                                     double2* __restrict__ acc, const double* __restrict__ am,
-                                     const double* __restrict__ ao) {
+// V0 = unit vectors e_J, J = (s0 + c) << js (zero elsewhere and in padding columns)
+__device__ __forceinline__ bool unit_at(int64_t K, int64_t col, int64_t D, int js) {
+  return col < (D >> js) && K == (col << js);
+}
+__global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, double2* __restrict__ V0, int64_t s0, int js) {
   const int64_t total = D * ldv;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t K = k / ldv, c = k - K * ldv;
-    V0[k] = make_double2(K == s0 + c ? 1.0 : 0.0, 0.0);
+    V0[k] = make_double2(unit_at(K, s0 + c, D, js) ? 1.0 : 0.0, 0.0);
   }
 }
 // FP32 pair-split layout: float4 (re_2p, re_2p+1, im_2p, im_2p+1)
-__global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, float4* __restrict__ V0, int64_t s0) {
+__global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, float4* __restrict__ V0, int64_t s0, int js) {
   const int64_t ldq = ldv / 2;
   const int64_t total = D * ldq;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t K = k / ldq, c = 2 * (k - K * ldq);
-    V0[k] = make_float4(K == s0 + c ? 1.f : 0.f, K == s0 + c + 1 ? 1.f : 0.f, 0.f, 0.f);
+    V0[k] = make_float4(unit_at(K, s0 + c, D, js) ? 1.f : 0.f, unit_at(K, s0 + c + 1, D, js) ? 1.f : 0.f, 0.f, 0.f);
   }
 }
-__global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, double2* __restrict__ acc,
+__global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, int js, double2* __restrict__ acc,
                                      const double* __restrict__ am, const double* __restrict__ ao) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ldv * kSlots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = k / kSlots;
     const int s = (int)(k - c * kSlots);
-    const int64_t J = s0 + c;
-    if (J >= D) continue;
+    if (s0 + c >= (D >> js)) continue;
+    const int64_t J = (s0 + c) << js;
     double2 a = make_double2(0.0, 0.0);
     if (s == 0) a.x = am[0];
     if (s == kSlots - 1) a.x = ao[0];
@@ -720,14 +727,14 @@ __global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, double2
 // acc += a_m V[local rows] (the last moment, which no step reads again)
 template <bool F32>
 __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const void* __restrict__ V,
-                                   int64_t s0, double2* __restrict__ acc, const double* __restrict__ am,
+                                   int64_t s0, int js, double2* __restrict__ acc, const double* __restrict__ am,
                                    const double* __restrict__ ao, int m) {
   const int64_t total = width * kSlots;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = k / kSlots;
     const int s = (int)(k - c * kSlots);
-    const int64_t J = s0 + c;
-    if (J >= D) continue;
+    if (s0 + c >= (D >> js)) continue;
+    const int64_t J = (s0 + c) << js;
     const int64_t j = J >> 1;
     const int beta = (int)(J & 1);
     const int xs = wrapi((int)(j % nx) + kSlotDx[s], nx);
@@ -776,7 +783,7 @@ cudaError_t launch_f32x2(const ChebPlan& p, const void* table, const void* Vprev
   const dim3 grid((p.ny + p.ylen2 - 1) / p.ylen2, (unsigned)(p.ldv / CB));
   cheb_step2_f32_kernel<CB><<<grid, p.nthreads, p.smem2, s>>>(
       p.nx, p.ny, p.D, p.ldv, p.ylen2, (const float2*)table, (const float4*)Vprev, (const float4*)Vcur,
-      (float4*)Vout1, (float4*)Vout2, s0, acc, am, ao, m);
+      (float4*)Vout1, (float4*)Vout2, s0, p.js, acc, am, ao, m);
   return cudaGetLastError();
 }
 
@@ -827,11 +834,11 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
   if (mode == 0)
     cheb_step_f32_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
                                                                  (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
-                                                                 s0, acc, am, ao, m);
+                                                                 s0, p.js, acc, am, ao, m);
   else
     cheb_step_f32_kernel<CB, 1><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
                                                                  (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
-                                                                 s0, acc, am, ao, m);
+                                                                 s0, p.js, acc, am, ao, m);
   return cudaGetLastError();
 }
 template <int CB>
@@ -840,12 +847,12 @@ cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, c
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
   if (mode == 0)
     cheb_step_kernel<double, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, acc, am,
-        ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, p.js, acc,
+        am, ao, m);
   else
     cheb_step_kernel<double, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, acc, am,
-        ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, p.js, acc,
+        am, ao, m);
   return cudaGetLastError();
 }
 
@@ -886,6 +893,7 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.cb2 = 0;
   p.ylen2 = 0;
   p.smem2 = 0;
+  p.js = 0;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the
@@ -960,13 +968,13 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
   const int64_t total = p.D * p.ldv;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 8 * kSMs * 4);
   if (precision == KPM_FP32)
-    cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (float4*)V0, s0);
+    cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (float4*)V0, s0, p.js);
   else
-    cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (double2*)V0, s0, acc, am, ao);
+    cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (double2*)V0, s0, p.js);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ga = (int)std::max<int64_t>(1, std::min<int64_t>((p.ldv * kSlots + 255) / 256, 4 * kSMs));
-  cheb_init_acc_kernel<<<ga, 256, 0, s>>>(p.D, p.ldv, s0, acc, am, ao);
+  cheb_init_acc_kernel<<<ga, 256, 0, s>>>(p.D, p.ldv, s0, p.js, acc, am, ao);
   return cudaGetLastError();
 }
 
@@ -1018,9 +1026,9 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
   const int64_t width = p.ldv;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((width * kSlots + 255) / 256, 4 * kSMs));
   if (precision == KPM_FP32)
-    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, acc, am, ao, m);
+    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, p.js, acc, am, ao, m);
   else
-    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, acc, am, ao, m);
+    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, p.js, acc, am, ao, m);
   return cudaGetLastError();
 }
 

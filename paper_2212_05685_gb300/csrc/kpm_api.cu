@@ -77,8 +77,8 @@ struct kpm_ctx {
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
 
-  // autotuned (block_width, cols_per_block, flags) per (nx, ny, precision)
-  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
+  // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass)
+  std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> tuned;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -198,12 +198,15 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
   const bool want_dbl = o->precision == KPM_FP32 && (o->flags & KPM_FLAG_DOUBLE_STEP);
-  int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, D) : D;
+  const int js = (o->flags & KPM_FLAG_PH_HALF) ? 1 : 0;
+  const int64_t ncols = D >> js;  // unit columns of the pass
+  int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, ncols) : ncols;
   if (o->block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((want_dbl ? 4 : 2) * (uint64_t)D * pp->elem));
-    width = balanced_width(D, std::min<int64_t>(width, std::max<int64_t>(fit, 1)));
+    width = balanced_width(ncols, std::min<int64_t>(width, std::max<int64_t>(fit, 1)));
   }
   pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
+  pp->cheb.js = js;
   if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
   // slabs advance by the padded width: every unit column belongs to exactly one slab
   pp->width = pp->cheb.ldv;
@@ -276,13 +279,14 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   int nl = 0, nr = 0;
   double nb = 0.0;
   const double vec = (double)p.D * (double)p.ldv * (double)pp.elem;  // bytes of one slab vector
-  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
+  const int64_t ncols = p.D >> p.js;
+  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
   else
     KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
   nl += 2;
-  for (int64_t s0 = 0; s0 < p.D; s0 += pp.width) {
+  for (int64_t s0 = 0; s0 < ncols; s0 += pp.width) {
     // X0 = V_{mm-1}, X1 = V_mm; Y0, Y1 the free pair of the double-step recursion
     void* X0 = ctx->slab[0];
     void* X1 = ctx->slab[1];
@@ -313,13 +317,13 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
       nb += 3 * vec;
       std::swap(X0, X1);
     }
-    if (events && s0 + pp.width >= p.D) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
+    if (events && s0 + pp.width >= ncols) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
     if (M >= 2) {
       KPM_CU(launch_cheb_gather(p, prec, X1, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
       nl += 1;
     }
   }
-  KPM_CU(launch_assemble(m->nx * m->ny, ctx->acc, ab, obs, omega, ctx->red, s));
+  KPM_CU(launch_assemble(m->nx, m->ny, ctx->acc, ab, obs, omega, ctx->red, s, p.js));
   nl += omega ? 2 : 1;
   if (launches) *launches = nl + nr;
   if (rec_launches) *rec_launches = nr;
@@ -338,6 +342,25 @@ int ensure_misc(kpm_ctx* ctx) {
     return fail(ctx, KPM_ENOMEM, "cudaMallocHost failed");
   }
   cudaMemset(ctx->misc, 0, 16 * sizeof(double));
+  return KPM_OK;
+}
+
+// KPM_FLAG_PH_HALF precondition: fields in the particle-hole symmetric sector
+// within 1e-12 of the largest field, and (ab given) |b| <= 1e-12 a.  Reads two
+// device scalars back, so it synchronises the stream.
+int check_ph_sector(kpm_ctx* ctx, const kpm_model* m, const double* fields, const double* ab, cudaStream_t s) {
+  int r;
+  if ((r = ensure_misc(ctx))) return r;
+  KPM_CU(launch_ph_asym(*m, fields, ctx->misc + 10, ctx->red, s));
+  KPM_CU(cudaMemcpyAsync(ctx->host_misc + 10, ctx->misc + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (ab) KPM_CU(cudaMemcpyAsync(ctx->host_misc + 12, ab, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  KPM_CU(cudaStreamSynchronize(s));
+  const double dev = ctx->host_misc[10], mag = ctx->host_misc[11];
+  if (!(dev <= 1e-12 * std::max(1.0, mag)))
+    return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: the fields are not particle-hole symmetric "
+                                 "(need eps_up = eps_dn, T_up = T_dn, D_ij = D_ji)");
+  if (ab && !(fabs(ctx->host_misc[13]) <= 1e-12 * ctx->host_misc[12]))
+    return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: the rescaling centre b must be 0");
   return KPM_OK;
 }
 
@@ -488,6 +511,9 @@ int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, 
   PassPlan pp;
   if ((r = plan_pass(ctx, model, opts, &pp))) return r;
   if ((r = ensure_pass_scratch(ctx, model, opts, pp))) return r;
+  if (opts->flags & KPM_FLAG_PH_HALF) {
+    if ((r = check_ph_sector(ctx, model, fields, ab, (cudaStream_t)stream))) return r;
+  }
   return enqueue_pass(ctx, model, opts, pp, fields, ab, obs, omega, (cudaStream_t)stream);
 }
 
@@ -520,6 +546,11 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   if (!params_dev) KPM_CU(cudaMemcpyAsync(dpar, params, 26 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s));
   if (!phi_dev) KPM_CU(cudaMemcpyAsync((void*)dphi, phi, 4 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s));
   if (!mu_dev) KPM_CU(cudaMemcpyAsync(dmu, mu_eff, sizeof(double), cudaMemcpyHostToDevice, s));
+  if (opts->flags & KPM_FLAG_PH_HALF) {
+    // the half pass keeps the sector exactly (spin-down observables are copies)
+    KPM_CU(launch_fields(*model, dphi, dpar, 0.0, ctx->fields, nullptr, s));
+    if ((r = check_ph_sector(ctx, model, ctx->fields, nullptr, s))) return r;
+  }
 
   kpm_ctx::Key key;
   memset(&key, 0, sizeof(key));
@@ -538,7 +569,8 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     int rr = KPM_OK;
     cudaError_t e = launch_fields(*model, dphi, dpar, 0.0, ctx->fields, nullptr, c);
     if (e == cudaSuccess) e = launch_shift_eps(N, ctx->fields, dmu, ctx->misc + 6, ctx->misc + 2, ctx->red, c);
-    if (e == cudaSuccess) e = launch_gershgorin(*model, ctx->fields, opts->margin, ab, ctx->red, c);
+    if (e == cudaSuccess)
+      e = launch_gershgorin(*model, ctx->fields, opts->margin, ab, ctx->red, c, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0);
     int npass = 0, nrec = 0;
     double nbytes = 0.0;
     if (e == cudaSuccess)
@@ -632,6 +664,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int K = M >= 2 ? (M - 1 + seg - 1) / seg : 0;  // segments, each serving m in [k seg + 1, (k+1) seg]
   const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
 
+  if (opts && (opts->flags & KPM_FLAG_PH_HALF)) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by kpm_backward");
   // slab width from the budget over all adjoint slab vectors (plus the forward pair);
   // the adjoint steps one moment per launch (its recomputed segments are stored)
   kpm_opts o = *opts;
@@ -741,6 +774,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       return fail(ctx, KPM_EINVAL, "mixing must lie in (0, 1]");
   }
   if ((r = check_dev(ctx, mu_eff, "mu_eff"))) return r;
+  if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by the batched call");
   if (opts->M < 1 || (opts->precision != KPM_FP32 && opts->precision != KPM_FP64))
     return fail(ctx, KPM_EINVAL, "bad opts");
   DeviceGuard g(ctx->device);
@@ -932,7 +966,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       const int N = models[c].nx * models[c].ny;
       const ChebPlan& p = plans[C.cls];
       if (M >= 2) KPM_TRY(launch_cheb_gather(p, prec, ((M - 1) & 1) ? C.B : C.A, 0, C.acc, C.am, C.ao, M - 1, c0));
-      KPM_TRY(launch_assemble(N, C.acc, C.misc, C.obs, C.misc + 3, ctx->bred, c0));
+      KPM_TRY(launch_assemble(models[c].nx, models[c].ny, C.acc, C.misc, C.obs, C.misc + 3, ctx->bred, c0));
       KPM_TRY(launch_update(N, params[c], C.obs, mu_eff + c, ropts[c], C.misc + 4, ctx->bred, c0));
       KPM_TRY(cudaMemcpyAsync(ctx->bhost + 16 * c, C.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c0));
     }
@@ -995,7 +1029,7 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int64_t D = 2 * (int64_t)N;
   const int prec = opts->precision;
   *best = *opts;
-  auto key = std::make_tuple(model->nx, model->ny, prec);
+  auto key = std::make_tuple(model->nx, model->ny, prec, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0);
   auto hit = ctx->tuned.find(key);
   if (hit != ctx->tuned.end()) {
     best->block_width = std::get<0>(hit->second);
@@ -1010,9 +1044,10 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   KPM_CU(cudaEventCreate(&e0));
   KPM_CU(cudaEventCreate(&e1));
   // candidates: full width and narrower slabs (down to L2-resident ones), every column chunk
-  std::vector<int64_t> widths = {D};
+  const int64_t ncols = (opts->flags & KPM_FLAG_PH_HALF) ? D / 2 : D;  // unit columns of a pass
+  std::vector<int64_t> widths = {ncols};
   for (int64_t w : {8192, 4096, 2048, 1024, 512, 384, 256, 128}) {
-    const int64_t bw = balanced_width(D, w);
+    const int64_t bw = balanced_width(ncols, w);
     if (bw < widths.back()) widths.push_back(bw);
   }
   std::vector<int> cols = prec == KPM_FP32 ? std::vector<int>{16, 8, 4} : std::vector<int>{8, 4, 2};
@@ -1024,7 +1059,7 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     for (int c : cols) for (int mode : modes) {
       kpm_opts o = *opts;
       o.M = Mt;
-      o.block_width = (int)std::min<int64_t>(w, D);
+      o.block_width = (int)w;
       o.cols_per_block = c;
       o.flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | mode;
       PassPlan pp;

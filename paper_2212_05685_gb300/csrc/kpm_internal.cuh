@@ -27,6 +27,9 @@ struct ChebPlan {
   int cb2;         // columns per CTA (divides cb)
   int ylen2;       // lattice rows per band
   size_t smem2;
+  // slab column c holds unit vector J = (s0 + c) << js (js = 1: particle-hole
+  // half pass over the columns (j, up) only; the pass covers D >> js columns)
+  int js;
 };
 
 // Per-cell pointers of a batch of equally shaped cells (FP32 recursion).
@@ -48,18 +51,22 @@ cudaError_t launch_fields(const kpm_model& m, const double* phi, const double* p
 // eps -= (mean(eps) + *mu_eff)   (mean over 2N site energies); mu_out = mu_eff + mean
 cudaError_t launch_shift_eps(int N, double* fields, const double* mu_eff, double* mean_scratch,
                              double* mu_out, double* red, cudaStream_t s);
+// symmetric: particle-hole symmetric spectrum, b = 0 and a = (1 + margin) max(hi, -lo)
 cudaError_t launch_gershgorin(const kpm_model& m, const double* fields, double margin, double* ab,
-                              double* red, cudaStream_t s);
-// a_m (step) and a^Omega_m coefficients from device (a, b)
-cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s);
+                              double* red, cudaStream_t s, int symmetric = 0);
+// out2 = {max deviation from eps_up = eps_dn, T_up = T_dn, D_ij = D_ji; max field modulus}
+cudaError_t launch_ph_asym(const kpm_model& m, const double* fields, double* out2, double* red, cudaStream_t s);
+// a_m (step) and a^Omega_m coefficients from device (a, b); half: a^Omega_m (1 + (-1)^m)
+cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half = 0);
 // per-site table of 2h~ entries in precision T (kCoef complex per site)
 cudaError_t launch_scale_table_f32(const kpm_model& m, const double* fields, const double* ab,
                                    float2* table, cudaStream_t s);
 cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, const double* ab,
                                    double2* table, cudaStream_t s);
 // obs from accumulators; omega = a * sum Re acc[J][9] (if omega != null)
-cudaError_t launch_assemble(int N, const double2* acc, const double* ab, double* obs, double* omega,
-                            double* red, cudaStream_t s);
+// half: particle-hole half pass (only the columns (j, up) accumulated)
+cudaError_t launch_assemble(int nx, int ny, const double2* acc, const double* ab, double* obs, double* omega,
+                            double* red, cudaStream_t s, int half = 0);
 // sum of a device array into *out (deterministic two-stage reduction)
 cudaError_t launch_sum(const double* x, int64_t n, double* out, double* red, cudaStream_t s);
 // RMFT mixing update; writes stats4 = {residual, density_error, -, -} and updates mu_eff

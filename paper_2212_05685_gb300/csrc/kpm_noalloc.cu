@@ -69,6 +69,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (!m || !o || !fields || !ab || !obs) return KPM_EINVAL;
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
+  if (o->flags & KPM_FLAG_PH_HALF) return KPM_EINVAL;  // the full pass only
   if (!is_device(fields) || !is_device(ab) || !is_device(obs) || (omega && !is_device(omega))) return KPM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -143,7 +144,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
     }
     if (M >= 2) KPM_NA(launch_cheb_gather(p, prec, ((M - 1) & 1) ? B : A, s0, acc, am, ao, M - 1, s));
   }
-  KPM_NA(launch_assemble(N, acc, ab, obs, omega, red, s));
+  KPM_NA(launch_assemble(m->nx, m->ny, acc, ab, obs, omega, red, s));
 #undef KPM_NA
   return KPM_OK;
 }

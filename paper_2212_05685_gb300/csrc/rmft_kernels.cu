@@ -376,7 +376,8 @@ __global__ void gershgorin_partial(kpm_model m, const double* __restrict__ fld, 
   }
 }
 
-__global__ void gershgorin_final(const double* __restrict__ part, int n, double margin, double* __restrict__ ab) {
+__global__ void gershgorin_final(const double* __restrict__ part, int n, double margin, int symmetric,
+                                 double* __restrict__ ab) {
   double hi = -INFINITY, lo = INFINITY;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     hi = fmax(hi, part[2 * k]);
@@ -385,9 +386,46 @@ __global__ void gershgorin_final(const double* __restrict__ part, int n, double 
   hi = block_reduce<1>(hi);
   lo = block_reduce<2>(lo);
   if (threadIdx.x == 0) {
-    const double half = 0.5 * (hi - lo);
-    ab[0] = half > 0.0 ? (1.0 + margin) * half : 1.0;
-    ab[1] = 0.5 * (hi + lo);
+    if (symmetric) {  // particle-hole symmetric spectrum: centre 0, half-width max(hi, -lo)
+      const double half = fmax(hi, -lo);
+      ab[0] = half > 0.0 ? (1.0 + margin) * half : 1.0;
+      ab[1] = 0.0;
+    } else {
+      const double half = 0.5 * (hi - lo);
+      ab[0] = half > 0.0 ? (1.0 + margin) * half : 1.0;
+      ab[1] = 0.5 * (hi + lo);
+    }
+  }
+}
+
+// Largest deviation of the fields from the particle-hole symmetric sector
+// (eps_up = eps_dn, T_up = T_dn, D_ij = D_ji) and the largest field modulus:
+// part[2 b] = deviation, part[2 b + 1] = modulus for block b.
+__global__ void ph_asym_partial(kpm_model m, const double* __restrict__ fld, double* __restrict__ part) {
+  const int nx = m.nx, ny = m.ny, N = nx * ny;
+  const Layout L{N};
+  double dev = 0.0, mag = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double e0 = L.n(fld, 0, i), e1 = L.n(fld, 1, i);
+    dev = fmax(dev, fabs(e0 - e1));
+    mag = fmax(mag, fmax(fabs(e0), fabs(e1)));
+    for (int d = 0; d < 4; ++d) {
+      const Cplx t0 = L.chi(fld, 0, d, i), t1 = L.chi(fld, 1, d, i);
+      dev = fmax(dev, cabs(cx(t0.re - t1.re, t0.im - t1.im)));
+      mag = fmax(mag, fmax(cabs(t0), cabs(t1)));
+    }
+    for (int e = 0; e < 4; ++e) {
+      const int j = shift(i, kNnX[e], kNnY[e], nx, ny);
+      const Cplx a = L.F(fld, e, i), b = L.F(fld, (e + 2) & 3, j);
+      dev = fmax(dev, cabs(cx(a.re - b.re, a.im - b.im)));
+      mag = fmax(mag, cabs(a));
+    }
+  }
+  dev = block_reduce<1>(dev);
+  mag = block_reduce<1>(mag);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = dev;
+    part[2 * blockIdx.x + 1] = mag;
   }
 }
 
@@ -398,8 +436,10 @@ __device__ double S_theta(int k, double th) {  // int_{th}^{pi} cos(k t) dt
   return k == 0 ? kPi - th : -sin(k * th) / k;
 }
 
+// half: particle-hole half pass, where the grand potential's diagonal moments of
+// the columns (j, dn) equal (-1)^m those of (j, up): a^Omega_m (1 + (-1)^m)
 __global__ void coefficients_kernel(int M, const double* __restrict__ ab, double* __restrict__ am,
-                                    double* __restrict__ ao) {
+                                    double* __restrict__ ao, int half) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   double x0 = -ab[1] / ab[0];
@@ -411,7 +451,7 @@ __global__ void coefficients_kernel(int M, const double* __restrict__ ab, double
   const double co = (0.5 * (S_theta(m + 1, th) + S_theta(m - 1, th)) - x0 * S_theta(m, th)) / kPi;
   const double w = m == 0 ? 1.0 : 2.0;
   am[m] = w * g * c;
-  ao[m] = w * g * co;
+  ao[m] = half ? ((m & 1) ? 0.0 : 2.0 * w * g * co) : w * g * co;
 }
 
 // Per-site table of 2h~ = 2(h - b)/a (App. B rescaling), neighbour order
@@ -471,29 +511,44 @@ __global__ void scale_table_kernel(kpm_model m, const double* __restrict__ fld, 
 // Observables from the accumulated entries of F_M(h~) e_J (readings N2, N3):
 //   column (j,0): n_up = acc[0], chi_up[d] = acc[1+d], F[e] = -conj(acc[5+e])
 //   column (j,1): n_dn = 1 - acc[0], chi_dn[d] = -conj(acc[1+d])
-__global__ void assemble_kernel(int N, const double2* __restrict__ acc, double* __restrict__ obs,
-                                double* __restrict__ part) {
+// half: only the columns (j,0) were propagated; in the particle-hole symmetric
+// sector F_M(h~) = 1 - U conj(F_M(h~)) U^T (U: (c_up, c^dag_dn) -> (c_dn,
+// -c^dag_up) per site), so column (j,1) gives n_dn = n_up, chi_dn = chi_up, and
+// acc[(j,0)][9] already holds both diagonal Omega moments.
+__global__ void assemble_kernel(int nx, int ny, const double2* __restrict__ acc, double* __restrict__ obs,
+                                double* __restrict__ part, int half) {
+  const int N = nx * ny;
   const Layout L{N};
   double om = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
     const double2* a0 = acc + (size_t)(2 * j) * kSlots;
     const double2* a1 = acc + (size_t)(2 * j + 1) * kSlots;
     *L.n_ptr(obs, 0, j) = a0[0].x;
-    *L.n_ptr(obs, 1, j) = 1.0 - a1[0].x;
+    *L.n_ptr(obs, 1, j) = half ? a0[0].x : 1.0 - a1[0].x;
     for (int d = 0; d < 4; ++d) {
       double* q0 = L.chi_ptr(obs, 0, d, j);
       q0[0] = a0[1 + d].x;
       q0[1] = a0[1 + d].y;
       double* q1 = L.chi_ptr(obs, 1, d, j);
-      q1[0] = -a1[1 + d].x;
-      q1[1] = a1[1 + d].y;
+      q1[0] = half ? a0[1 + d].x : -a1[1 + d].x;
+      q1[1] = half ? a0[1 + d].y : a1[1 + d].y;
     }
     for (int e = 0; e < 4; ++e) {
       double* q = L.F_ptr(obs, e, j);
-      q[0] = -a0[5 + e].x;
-      q[1] = a0[5 + e].y;
+      if (half) {
+        // singlet sector: F_{j,j+e} = F_{j+e,j}; the two estimates (columns
+        // (j, up) and (j+e, up)) are averaged, which keeps the state exactly in
+        // the sector the half pass assumes
+        const int k = shift(j, kNnX[e], kNnY[e], nx, ny);
+        const double2 b = acc[(size_t)(2 * k) * kSlots + 5 + ((e + 2) & 3)];
+        q[0] = 0.5 * (-a0[5 + e].x - b.x);
+        q[1] = 0.5 * (a0[5 + e].y + b.y);
+      } else {
+        q[0] = -a0[5 + e].x;
+        q[1] = a0[5 + e].y;
+      }
     }
-    om += a0[9].x + a1[9].x;
+    om += half ? a0[9].x : a0[9].x + a1[9].x;
   }
   om = block_reduce<0>(om);
   if (threadIdx.x == 0) part[blockIdx.x] = om;
@@ -618,16 +673,38 @@ cudaError_t launch_shift_eps(int N, double* fields, const double* mu_eff, double
 }
 
 cudaError_t launch_gershgorin(const kpm_model& m, const double* fields, double margin, double* ab, double* red,
-                              cudaStream_t s) {
+                              cudaStream_t s, int symmetric) {
   const int N = m.nx * m.ny;
   const int g = grid_for(N);
   gershgorin_partial<<<g, kRedBlock, 0, s>>>(m, fields, red);
-  gershgorin_final<<<1, kRedBlock, 0, s>>>(red, g, margin, ab);
+  gershgorin_final<<<1, kRedBlock, 0, s>>>(red, g, margin, symmetric, ab);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s) {
-  coefficients_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, ab, am, ao);
+__global__ void ph_asym_final(const double* __restrict__ part, int n, double* __restrict__ out) {
+  double dev = 0.0, mag = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    dev = fmax(dev, part[2 * k]);
+    mag = fmax(mag, part[2 * k + 1]);
+  }
+  dev = block_reduce<1>(dev);
+  mag = block_reduce<1>(mag);
+  if (threadIdx.x == 0) {
+    out[0] = dev;
+    out[1] = mag;
+  }
+}
+
+cudaError_t launch_ph_asym(const kpm_model& m, const double* fields, double* out2, double* red, cudaStream_t s) {
+  const int N = m.nx * m.ny;
+  const int g = grid_for(N);
+  ph_asym_partial<<<g, kRedBlock, 0, s>>>(m, fields, red);
+  ph_asym_final<<<1, kRedBlock, 0, s>>>(red, g, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half) {
+  coefficients_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, ab, am, ao, half);
   return cudaGetLastError();
 }
 
@@ -645,10 +722,10 @@ cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(int N, const double2* acc, const double* ab, double* obs, double* omega, double* red,
-                            cudaStream_t s) {
-  const int g = grid_for(N);
-  assemble_kernel<<<g, kRedBlock, 0, s>>>(N, acc, obs, red);
+cudaError_t launch_assemble(int nx, int ny, const double2* acc, const double* ab, double* obs, double* omega,
+                            double* red, cudaStream_t s, int half) {
+  const int g = grid_for(nx * ny);
+  assemble_kernel<<<g, kRedBlock, 0, s>>>(nx, ny, acc, obs, red, half);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess || omega == nullptr) return err;
   // omega = a * sum Re acc[J][9]; a read on the device

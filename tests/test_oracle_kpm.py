@@ -81,6 +81,34 @@ def test_particle_hole_symmetric_sector():
         assert np.max(np.abs(F[e] - F[(e + 2) % 4][j])) < 1e-12
 
 
+def test_particle_hole_half_relations():
+    """What the particle-hole half pass relies on: in the symmetric sector
+    (b = 0) the damped step series obeys F_M(h~) = 1 - U conj(F_M(h~)) U^T, i.e.
+    entry ((k,dn),(j,dn)) = delta_kj - conj(entry ((k,up),(j,up))), and the
+    grand potential's (j,dn) diagonal equals the (j,up) diagonal of G_M(-h~)."""
+    model, p, fld = _setup(6, 5, 0, sym=True)
+    h = bdg.dense(model, fld)
+    a, b = bdg.gershgorin(model, fld)
+    M = 96
+    F1, _ = kpm.f_spectral(h, a, b, M)
+    up, dn = np.arange(0, h.shape[0], 2), np.arange(1, h.shape[0], 2)
+    lhs = F1[np.ix_(dn, dn)]
+    rhs = np.eye(model.N) - np.conj(F1[np.ix_(up, up)])
+    assert np.max(np.abs(lhs - rhs)) < 1e-12
+    # F_M((k,up),(j,dn)) = conj(F_M((k,dn),(j,up))) elementwise
+    assert np.max(np.abs(F1[np.ix_(up, dn)] - np.conj(F1[np.ix_(dn, up)]))) < 1e-12
+    E, U = np.linalg.eigh(h)
+    x = (E - b) / a
+    _, ao = kpm.coefficients(M, a, b)
+    w = np.abs(U) ** 2
+    g_dn = w[dn] @ kpm.cheb_eval(ao, x)
+    g_up_reflected = w[up] @ kpm.cheb_eval(ao, -x)
+    assert np.max(np.abs(g_dn - g_up_reflected)) < 1e-12
+    # so the sum over the (j,dn) diagonals uses the coefficients (-1)^m a^Omega_m
+    signs = (-1.0) ** np.arange(M)
+    assert np.max(np.abs(g_dn - w[up] @ kpm.cheb_eval(signs * ao, x))) < 1e-12
+
+
 def test_kpm_converges_to_ground_state_with_M():
     # a gapped uniform d-wave state: exponential convergence of F_M to theta
     model = rmft.Model(12, 12, flux=0)
