@@ -360,10 +360,10 @@ def run_ours(args):
     pk, pk_kind = peaks()
     achieved = rec_bytes / (rec_ms / 1e3) / 1e9
     nslab = 4 if dbl else 2
-    # the committed ncu counters were taken on a slab larger than L2; they
-    # scale to full-width slabs only
+    # the committed ncu counters were taken on a 2000-column slab (both slab
+    # vectors larger than L2); they scale by columns to any slab that is too
     traffic = measured_traffic("cheb_step2_fp32_100x100.json" if dbl else "cheb_step_fp32_100x100.json",
-                               kernel_hash(), ldv) if width == D else None
+                               kernel_hash(), ldv) if 2 * D * ldv * 8 > 129e6 else None
 
     fp64 = None
     if not args.no_fp64:
@@ -606,7 +606,7 @@ def profile_adjoint(full=False):
     return 0
 
 
-def profile_small():
+def profile_small(double_step=False):
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
     (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
     import torch
@@ -624,7 +624,8 @@ def profile_small():
     obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
     kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
     kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
-    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000), fields, ab, obs)
+    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000,
+                                                  flags=kpm.KPM_FLAG_DOUBLE_STEP if double_step else 0), fields, ab, obs)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(obs).all())
     kpm.kpm_destroy(ctx)
@@ -635,7 +636,7 @@ def profile_small():
 def main():
     args = parse()
     if args.profile_small:
-        return profile_small()
+        return profile_small(args.double_step)
     if args.profile_adjoint:
         return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":
