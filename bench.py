@@ -66,6 +66,30 @@ def dist_env():
     return world, rank, local
 
 
+def rank_cell(rank):
+    """The benchmark cell of one rank: the 100x100 workload with its own seed
+    (independent problems per GPU, weak scaling, no data-path collective)."""
+    import dataclasses
+    from paper_2212_05685_gb300 import inputs
+    return dataclasses.replace(inputs.CFG2, seed=inputs.CFG2.seed + rank)
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, units_per_step, seconds):
+    """Whole-job throughput: the units all ranks processed / the job time."""
+    return world * steps * units_per_step / seconds
+
+
 # ----------------------------------------------------------------------------- clocks
 
 FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -253,8 +277,7 @@ def run_ours(args):
         dist.barrier()
     kpm.load()
 
-    import dataclasses
-    w = dataclasses.replace(inputs.CFG2, seed=inputs.CFG2.seed + rank)
+    w = rank_cell(rank)
     N, D, M = w.n_sites, w.dim, w.M
     stream = torch.cuda.current_stream()
     ctx = kpm.kpm_create(local)
@@ -305,12 +328,8 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * args.steps * D * M / t
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, "cuda")
+    value = job_value(world, args.steps, D * M, t)
 
     # end to end through the public call with pinned host buffers: the step's
     # parameters (and phases) go host->device, the updated parameters and the
@@ -328,12 +347,8 @@ def run_ours(args):
         for _ in range(args.steps):
             kpm.rmft_iterate(ctx, model, opts, ropts, hphi, hp, hmu, 1)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world * args.steps * D * M / te, "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": job_value(world, args.steps, D * M, te), "unit": UNIT,
                "h2d_bytes_per_step": (26 * N + 4 * N + 1) * 8,
                "d2h_bytes_per_step": (26 * N + 1) * 8 + 8 * 8}
 
