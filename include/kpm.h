@@ -76,6 +76,14 @@ typedef struct {
   int32_t cols_per_block; /* columns per CTA in the recursion kernel; 0 = default */
   double margin;        /* spectral half-width margin of the Gershgorin rescale (0.01) */
   int32_t flags;        /* KPM_FLAG_* bits; 0 = defaults */
+  int32_t probe_p;      /* 0: all unit start vectors (exact trace).  p >= 2, dividing nx
+                           and ny: R = 2 p^2 probing vectors (App. B): Nambu row
+                           K = 2 i + alpha of site (x, y) has colour alpha + 2 ((x mod
+                           p) + p (y mod p)) and phase xi_K = exp(2 pi i u_K), u_K from
+                           SplitMix64 at counter probe_seed * 2^32 + K; column J of
+                           F_M(h~) is estimated as conj(xi_J) F_M(h~) r_colour(J).
+                           kpm_observables and rmft_iterate only. */
+  int32_t probe_seed;   /* phase stream of the probing vectors */
   int32_t reserved;     /* 0 */
 } kpm_opts;
 
@@ -183,7 +191,7 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
  * or two steps per launch, and writes the fastest (block_width,
  * cols_per_block, KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields
  * copied from *opts).  Results are cached per (nx, ny, precision,
- * KPM_FLAG_PH_HALF) in the context
+ * KPM_FLAG_PH_HALF, probe_p) in the context
  * (a cached answer returns *best_ms_per_step = -1).  fields, ab: device, as
  * for kpm_observables.  best_ms_per_step: host double or NULL. */
 int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,

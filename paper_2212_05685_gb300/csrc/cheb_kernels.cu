@@ -7,7 +7,10 @@
 // rows K_s(J) of every column (and the grand-potential series on the diagonal)
 // fused into the step that reads V_m (Eqs. rho_KPM, F_KPM with unit r).
 // Slab column c holds the unit vector of row J = (s0 + c) << js: js = 0 all
-// D columns, js = 1 only the columns (j, up) of the particle-hole half pass.
+// D columns, js = 1 only the columns (j, up) of the particle-hole half pass;
+// or (probing, App. B) the vector r_{s0+c} of colour s0 + c, whose entries are
+// the phases xi_K on the rows of that colour; then every row J is a source
+// whose column estimate conj(xi_J) F_M(h~) r_colour(J) is summed.
 //
 // Layout: V is row-major, V[K][c] with K = 2 i + alpha the Nambu row and c the
 // column inside the slab; the row stride ldv is the slab width rounded up to
@@ -78,6 +81,62 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Probing vectors (App. B): colour of Nambu row K = 2 i + alpha, i = (x, y),
+// alpha + 2 ((x mod p) + p (y mod p)); phase xi_K = exp(2 pi i u_K) with u_K
+// from the counter-based generator SplitMix64 (Steele, Lea and Flood 2014) at
+// counter seed * 2^32 + K.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ double2 probe_xi(uint32_t seed, int64_t K) {
+  const double u = (double)(splitmix64(((uint64_t)seed << 32) + (uint64_t)K) >> 11) * 0x1.0p-53;
+  double sn, cs;
+  sincospi(2.0 * u, &sn, &cs);
+  return make_double2(cs, sn);
+}
+__device__ __forceinline__ int probe_colour(int64_t K, int nx, int p) {
+  const int64_t i = K >> 1;
+  const int x = (int)(i % nx), y = (int)(i / nx);
+  return (int)(K & 1) + 2 * ((x % p) + p * (y % p));
+}
+
+// Moment-sum items of lattice row y for the chunk's columns [cb0, cb0 + CB):
+// unit vectors: item t = c * kSlots + s over the chunk's columns; probing:
+// t = r * kSlots + s over the 2 nx rows of lattice row y.  False when the item
+// has no source here; else the source row J, its chunk column c, the slot s
+// and the weight conj(xi_J) (1 for unit vectors).
+__device__ __forceinline__ int source_items(const ColMap& cm, int nx, int CB) {
+  return (cm.probe_p ? 2 * nx : CB) * kSlots;
+}
+__device__ __forceinline__ bool source_item(const ColMap& cm, int t, int y, int nx, int64_t D, int64_t cb0, int CB,
+                                            int64_t& J, int& c, int& s, double2& wgt) {
+  s = t % kSlots;
+  const int r = t / kSlots;
+  if (cm.probe_p) {
+    J = 2 * (int64_t)y * nx + r;
+    const int64_t col = probe_colour(J, nx, cm.probe_p) - cm.s0 - cb0;
+    if (col < 0 || col >= CB) return false;
+    c = (int)col;
+    const double2 xi = probe_xi(cm.seed, J);
+    wgt = make_double2(xi.x, -xi.y);
+    return true;
+  }
+  const int64_t col = cm.s0 + cb0 + r;
+  if (col >= (D >> cm.js)) return false;
+  J = col << cm.js;
+  if ((J >> 1) / nx != y) return false;
+  c = r;
+  wgt = make_double2(1.0, 0.0);
+  return true;
+}
+__device__ __forceinline__ void acc_add(double2* a, double coef, double2 w, double vr, double vi) {
+  a->x += coef * (w.x * vr - w.y * vi);
+  a->y += coef * (w.x * vi + w.y * vr);
+}
+
 // one lattice row of V (2 nx Nambu rows x CB columns) into shared memory
 template <typename C, int CB>
 __device__ __forceinline__ void stage_row(C* dst, const C* __restrict__ V, int ly, int nx, int64_t ldv,
@@ -105,7 +164,7 @@ template <typename Real, int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const typename CT<Real>::C* __restrict__ table,
                      const typename CT<Real>::C* __restrict__ Vcur, const typename CT<Real>::C* Vprev,
-                     typename CT<Real>::C* Vout, int64_t s0, int js, double2* __restrict__ acc,
+                     typename CT<Real>::C* Vout, ColMap cmap, double2* __restrict__ acc,
                      const double* __restrict__ am, const double* __restrict__ ao, int m) {
   using C = typename CT<Real>::C;
   using V = typename CT<Real>::V;
@@ -196,23 +255,20 @@ __global__ void __launch_bounds__(512, 1)
     if (MODE == 1 && acc != nullptr) {
       // moment sums of the columns whose own site lies in lattice row y
       const double cm = am[m], co = ao[m];
-      for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
-        const int c = t / kSlots, s = t - c * kSlots;
-        const int64_t col = s0 + cb0 + c;
-        if (col >= (D >> js)) continue;
-        const int64_t J = col << js;
+      const int items = source_items(cmap, nx, CB);
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        int64_t J;
+        int c, s;
+        double2 wgt;
+        if (!source_item(cmap, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
         const int64_t j = J >> 1;
-        if (j / nx != y) continue;
         const int beta = (int)(J & 1);
         const int xs = wrapi((int)(j % nx) + kSlotDx[s], nx);
         const int dy = kSlotDy[s];
         const C* w = dy < 0 ? wm : (dy > 0 ? wp : w0);
         const int al = kSlotFlip[s] ? 1 - beta : beta;
         const C val = w[(2 * xs + al) * CB + c];
-        const double coef_m = s == kSlots - 1 ? co : cm;
-        double2* a = acc + J * kSlots + s;
-        a->x += coef_m * (double)val.x;
-        a->y += coef_m * (double)val.y;
+        acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
       }
     }
     __syncthreads();
@@ -329,27 +385,24 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
 // own site lies in lattice row y; wm, w0, wp hold rows y-1, y, y+1
 template <int CB, bool SW = false>
 __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, const float4* wp, int nx, int y,
-                                            int64_t D, int64_t s0, int js, int64_t cb0, double cm, double co,
+                                            int64_t D, const ColMap& cmap, int64_t cb0, double cm, double co,
                                             double2* __restrict__ acc) {
   constexpr int NV = CB / 2;
   constexpr int RS = 2 * NV;
-  for (int t = threadIdx.x; t < CB * kSlots; t += blockDim.x) {
-    const int c = t / kSlots, s = t - c * kSlots;
-    const int64_t col = s0 + cb0 + c;
-    if (col >= (D >> js)) continue;
-    const int64_t J = col << js;
+  const int items = source_items(cmap, nx, CB);
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
+    int64_t J;
+    int c, s;
+    double2 wgt;
+    if (!source_item(cmap, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
     const int64_t j = J >> 1;
-    if (j / nx != y) continue;
     const int beta = (int)(J & 1);
     const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
     const int dy = kSlotDy[s];
     const float4* w = dy < 0 ? wm : (dy > 0 ? wp : w0);
     const int al = kSlotFlip[s] ? 1 - beta : beta;
     const float2 val = pair_elem(w + xsl * RS + nambu_slot<NV, SW>(xsl, al) * NV, c);
-    const double coef_m = s == kSlots - 1 ? co : cm;
-    double2* a = acc + J * kSlots + s;
-    a->x += coef_m * (double)val.x;
-    a->y += coef_m * (double)val.y;
+    acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
   }
 }
 
@@ -373,7 +426,7 @@ __device__ __forceinline__ void stage_row_sw(float4* dst, const float4* __restri
 template <int CB, int MODE>
 __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
                                               const float2* __restrict__ table, const float4* __restrict__ Vcur,
-                                              const float4* Vprev, float4* Vout, int64_t s0, int js,
+                                              const float4* Vprev, float4* Vout, ColMap cmap,
                                               double2* __restrict__ acc,
                                               const double* __restrict__ am, const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;   // float4 (column pairs) per Nambu row of the chunk
@@ -400,10 +453,13 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
   // rows of the chunk's own sites: only there are moment sums due
   int yj_lo = ny, yj_hi = -1;
   {
-    const int64_t clo = s0 + cb0, chi = min(D >> js, s0 + cb0 + CB) - 1;
-    if (chi >= clo) {
-      yj_lo = (int)(((clo << js) >> 1) / nx);
-      yj_hi = (int)(((chi << js) >> 1) / nx);
+    const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
+    if (cmap.probe_p) {  // every lattice row holds sources of every colour class
+      yj_lo = 0;
+      yj_hi = ny - 1;
+    } else if (chi >= clo) {
+      yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
+      yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
     }
   }
 
@@ -479,7 +535,7 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
     }
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
-      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, s0, js, cb0, am[m], ao[m], acc);
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, am[m], ao[m], acc);
     bm = b0;
     bc = bc + 1 == 3 ? 0 : bc + 1;
     if (MODE == 1) {
@@ -495,10 +551,10 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
 template <int CB, int MODE>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
-                         const float4* __restrict__ Vcur, const float4* Vprev, float4* Vout, int64_t s0, int js,
+                         const float4* __restrict__ Vcur, const float4* Vprev, float4* Vout, ColMap cmap,
                          double2* __restrict__ acc, const double* __restrict__ am, const double* __restrict__ ao,
                          int m) {
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, s0, js, acc, am, ao, m);
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, cmap, acc, am, ao, m);
 }
 
 // FP32 double step: two recursion steps per launch (Eq. alpha applied twice),
@@ -518,7 +574,7 @@ template <int CB>
 __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_t ldv, int ylen,
                                                const float2* __restrict__ table, const float4* __restrict__ Vprev,
                                                const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
-                                               float4* __restrict__ Vout2, int64_t s0, int js,
+                                               float4* __restrict__ Vout2, ColMap cmap,
                                                double2* __restrict__ acc, const double* __restrict__ am,
                                                const double* __restrict__ ao, int m) {
   constexpr int NV = CB / 2;
@@ -546,10 +602,13 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
 
   int yj_lo = ny, yj_hi = -1;
   {
-    const int64_t clo = s0 + cb0, chi = min(D >> js, s0 + cb0 + CB) - 1;
-    if (chi >= clo) {
-      yj_lo = (int)(((clo << js) >> 1) / nx);
-      yj_hi = (int)(((chi << js) >> 1) / nx);
+    const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
+    if (cmap.probe_p) {  // every lattice row holds sources of every colour class
+      yj_lo = 0;
+      yj_hi = ny - 1;
+    } else if (chi >= clo) {
+      yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
+      yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
     }
   }
   auto stage_v = [&](float4* dst, int ly) {
@@ -627,7 +686,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         }
       }
       if (acc != nullptr && f >= y0 && f < y1 && f >= yj_lo && f <= yj_hi)
-        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, s0, js, cb0, am[m], ao[m], acc);
+        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, cmap, cb0, am[m], ao[m], acc);
     }
     __syncthreads();
 
@@ -654,7 +713,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         *reinterpret_cast<ulonglong2*>(gp + ldq) = o1;
       }
       if (acc != nullptr && g >= yj_lo && g <= yj_hi)
-        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, s0, js, cb0, am[m + 1], ao[m + 1], acc);
+        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, cmap, cb0, am[m + 1], ao[m + 1], acc);
     }
     pc[0][0] = pn[0][0];
     pc[0][1] = pn[0][1];
@@ -668,9 +727,9 @@ template <int CB>
 __global__ void __launch_bounds__(512, 1)
     cheb_step2_f32_kernel(int nx, int ny, int64_t D, int64_t ldv, int ylen, const float2* __restrict__ table,
                           const float4* __restrict__ Vprev, const float4* __restrict__ Vcur, float4* __restrict__ Vout1,
-                          float4* __restrict__ Vout2, int64_t s0, int js, double2* __restrict__ acc,
+                          float4* __restrict__ Vout2, ColMap cmap, double2* __restrict__ acc,
                           const double* __restrict__ am, const double* __restrict__ ao, int m) {
-  f32_step2_body<CB>(nx, ny, D, ldv, ylen, table, Vprev, Vcur, Vout1, Vout2, s0, js, acc, am, ao, m);
+  f32_step2_body<CB>(nx, ny, D, ldv, ylen, table, Vprev, Vcur, Vout1, Vout2, cmap, acc, am, ao, m);
 }
 
 // Batched step: cells of one shape, blockIdx.z selects the cell; every cell
@@ -685,38 +744,57 @@ __global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, i
     cur = reinterpret_cast<const float4*>(b.A[z]);
     out = reinterpret_cast<float4*>(b.B[z]);
   }
-  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out, 0, 0,
-                          b.acc[z], b.am[z], b.ao[z], m);
+  f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out,
+                          ColMap{0, 0, 0, 0u}, b.acc[z], b.am[z], b.ao[z], m);
 }
 
-// V0 = unit vectors e_J, J = (s0 + c) << js (zero elsewhere and in padding columns)
-__device__ __forceinline__ bool unit_at(int64_t K, int64_t col, int64_t D, int js) {
-  return col < (D >> js) && K == (col << js);
+// V0: entry (K, c) of the start vector held by slab column c (unit vector
+// e_{(s0+c) << js}, or probing vector r_{s0+c}); zero in padding columns
+__device__ __forceinline__ double2 start_entry(int64_t K, int64_t c, int64_t D, int nx, const ColMap& cm) {
+  const int64_t col = cm.s0 + c;
+  if (cm.probe_p) {
+    if (col >= 2 * (int64_t)cm.probe_p * cm.probe_p || probe_colour(K, nx, cm.probe_p) != col)
+      return make_double2(0.0, 0.0);
+    return probe_xi(cm.seed, K);
+  }
+  return make_double2(col < (D >> cm.js) && K == (col << cm.js) ? 1.0 : 0.0, 0.0);
 }
-__global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, double2* __restrict__ V0, int64_t s0, int js) {
+__global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, int nx, double2* __restrict__ V0, ColMap cm) {
   const int64_t total = D * ldv;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t K = k / ldv, c = k - K * ldv;
-    V0[k] = make_double2(unit_at(K, s0 + c, D, js) ? 1.0 : 0.0, 0.0);
+    V0[k] = start_entry(K, c, D, nx, cm);
   }
 }
 // FP32 pair-split layout: float4 (re_2p, re_2p+1, im_2p, im_2p+1)
-__global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, float4* __restrict__ V0, int64_t s0, int js) {
+__global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, int nx, float4* __restrict__ V0, ColMap cm) {
   const int64_t ldq = ldv / 2;
   const int64_t total = D * ldq;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t K = k / ldq, c = 2 * (k - K * ldq);
-    V0[k] = make_float4(unit_at(K, s0 + c, D, js) ? 1.f : 0.f, unit_at(K, s0 + c + 1, D, js) ? 1.f : 0.f, 0.f, 0.f);
+    const double2 e0 = start_entry(K, c, D, nx, cm), e1 = start_entry(K, c + 1, D, nx, cm);
+    V0[k] = make_float4((float)e0.x, (float)e1.x, (float)e0.y, (float)e1.y);
   }
 }
-__global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, int js, double2* __restrict__ acc,
+// the m = 0 moment terms of every source of the slab: a_0 on the own-row slot
+// and a^Omega_0 on the diagonal slot (the local rows of a source never share
+// its probing colour, so conj(xi_J) V_0 is 1 on row J and 0 on the others)
+__global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int nx, ColMap cm, double2* __restrict__ acc,
                                      const double* __restrict__ am, const double* __restrict__ ao) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ldv * kSlots;
+  const int64_t nsrc = cm.probe_p ? D : ldv;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nsrc * kSlots;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = k / kSlots;
-    const int s = (int)(k - c * kSlots);
-    if (s0 + c >= (D >> js)) continue;
-    const int64_t J = (s0 + c) << js;
+    const int64_t r = k / kSlots;
+    const int s = (int)(k - r * kSlots);
+    int64_t J;
+    if (cm.probe_p) {
+      const int64_t col = probe_colour(r, nx, cm.probe_p) - cm.s0;
+      if (col < 0 || col >= ldv) continue;
+      J = r;
+    } else {
+      if (cm.s0 + r >= (D >> cm.js)) continue;
+      J = (cm.s0 + r) << cm.js;
+    }
     double2 a = make_double2(0.0, 0.0);
     if (s == 0) a.x = am[0];
     if (s == kSlots - 1) a.x = ao[0];
@@ -727,14 +805,25 @@ __global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int64_t s0, int js,
 // acc += a_m V[local rows] (the last moment, which no step reads again)
 template <bool F32>
 __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const void* __restrict__ V,
-                                   int64_t s0, int js, double2* __restrict__ acc, const double* __restrict__ am,
+                                   ColMap cm, double2* __restrict__ acc, const double* __restrict__ am,
                                    const double* __restrict__ ao, int m) {
-  const int64_t total = width * kSlots;
+  const int64_t total = (cm.probe_p ? D : width) * kSlots;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = k / kSlots;
-    const int s = (int)(k - c * kSlots);
-    if (s0 + c >= (D >> js)) continue;
-    const int64_t J = (s0 + c) << js;
+    const int64_t r = k / kSlots;
+    const int s = (int)(k - r * kSlots);
+    int64_t J, c;
+    double2 wgt = make_double2(1.0, 0.0);
+    if (cm.probe_p) {
+      J = r;
+      c = probe_colour(J, nx, cm.probe_p) - cm.s0;
+      if (c < 0 || c >= width) continue;
+      const double2 xi = probe_xi(cm.seed, J);
+      wgt = make_double2(xi.x, -xi.y);
+    } else {
+      c = r;
+      if (cm.s0 + c >= (D >> cm.js)) continue;
+      J = (cm.s0 + c) << cm.js;
+    }
     const int64_t j = J >> 1;
     const int beta = (int)(J & 1);
     const int xs = wrapi((int)(j % nx) + kSlotDx[s], nx);
@@ -751,10 +840,7 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
       re = val.x;
       im = val.y;
     }
-    const double cf = s == kSlots - 1 ? ao[m] : am[m];
-    double2* a = acc + J * kSlots + s;
-    a->x += cf * re;
-    a->y += cf * im;
+    acc_add(acc + J * kSlots + s, s == kSlots - 1 ? ao[m] : am[m], wgt, re, im);
   }
 }
 
@@ -783,7 +869,7 @@ cudaError_t launch_f32x2(const ChebPlan& p, const void* table, const void* Vprev
   const dim3 grid((p.ny + p.ylen2 - 1) / p.ylen2, (unsigned)(p.ldv / CB));
   cheb_step2_f32_kernel<CB><<<grid, p.nthreads, p.smem2, s>>>(
       p.nx, p.ny, p.D, p.ldv, p.ylen2, (const float2*)table, (const float4*)Vprev, (const float4*)Vcur,
-      (float4*)Vout1, (float4*)Vout2, s0, p.js, acc, am, ao, m);
+      (float4*)Vout1, (float4*)Vout2, colmap(p, s0), acc, am, ao, m);
   return cudaGetLastError();
 }
 
@@ -834,11 +920,11 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
   if (mode == 0)
     cheb_step_f32_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
                                                                  (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
-                                                                 s0, p.js, acc, am, ao, m);
+                                                                 colmap(p, s0), acc, am, ao, m);
   else
     cheb_step_f32_kernel<CB, 1><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
                                                                  (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
-                                                                 s0, p.js, acc, am, ao, m);
+                                                                 colmap(p, s0), acc, am, ao, m);
   return cudaGetLastError();
 }
 template <int CB>
@@ -847,12 +933,12 @@ cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, c
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
   if (mode == 0)
     cheb_step_kernel<double, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, p.js, acc,
-        am, ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout,
+        colmap(p, s0), acc, am, ao, m);
   else
     cheb_step_kernel<double, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
-        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout, s0, p.js, acc,
-        am, ao, m);
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const double2*)table, (const double2*)Vcur, (const double2*)Vprev, (double2*)Vout,
+        colmap(p, s0), acc, am, ao, m);
   return cudaGetLastError();
 }
 
@@ -894,6 +980,8 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.ylen2 = 0;
   p.smem2 = 0;
   p.js = 0;
+  p.probe_p = 0;
+  p.probe_seed = 0;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the
@@ -968,13 +1056,13 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
   const int64_t total = p.D * p.ldv;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 8 * kSMs * 4);
   if (precision == KPM_FP32)
-    cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (float4*)V0, s0, p.js);
+    cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, p.nx, (float4*)V0, colmap(p, s0));
   else
-    cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, (double2*)V0, s0, p.js);
+    cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, p.nx, (double2*)V0, colmap(p, s0));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ga = (int)std::max<int64_t>(1, std::min<int64_t>((p.ldv * kSlots + 255) / 256, 4 * kSMs));
-  cheb_init_acc_kernel<<<ga, 256, 0, s>>>(p.D, p.ldv, s0, p.js, acc, am, ao);
+  cheb_init_acc_kernel<<<ga, 256, 0, s>>>(p.D, p.ldv, p.nx, colmap(p, s0), acc, am, ao);
   return cudaGetLastError();
 }
 
@@ -1026,9 +1114,10 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
   const int64_t width = p.ldv;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((width * kSlots + 255) / 256, 4 * kSMs));
   if (precision == KPM_FP32)
-    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, p.js, acc, am, ao, m);
+    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao, m);
   else
-    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, s0, p.js, acc, am, ao, m);
+    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao,
+                                                   m);
   return cudaGetLastError();
 }
 

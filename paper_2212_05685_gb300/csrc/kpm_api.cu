@@ -77,8 +77,8 @@ struct kpm_ctx {
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
 
-  // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass)
-  std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> tuned;
+  // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass, probe_p)
+  std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> tuned;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -197,9 +197,15 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
-  const bool want_dbl = o->precision == KPM_FP32 && (o->flags & KPM_FLAG_DOUBLE_STEP);
+  const int pp_ = o->probe_p;
+  if (pp_ < 0 || pp_ == 1 || (pp_ > 0 && (m->nx % pp_ != 0 || m->ny % pp_ != 0)))
+    return fail(ctx, KPM_EINVAL, "probe_p must be 0 or >= 2 and divide nx and ny");
+  if (pp_ > 0 && (o->flags & KPM_FLAG_PH_HALF))
+    return fail(ctx, KPM_EINVAL, "probing and KPM_FLAG_PH_HALF do not combine");
+  const bool want_dbl = o->precision == KPM_FP32 && (o->flags & KPM_FLAG_DOUBLE_STEP) && pp_ == 0;
   const int js = (o->flags & KPM_FLAG_PH_HALF) ? 1 : 0;
-  const int64_t ncols = D >> js;  // unit columns of the pass
+  // start vectors of the pass: unit columns, or R = 2 p^2 probing vectors
+  const int64_t ncols = pp_ > 0 ? std::min<int64_t>(D, 2 * (int64_t)pp_ * pp_) : (D >> js);
   int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, ncols) : ncols;
   if (o->block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((want_dbl ? 4 : 2) * (uint64_t)D * pp->elem));
@@ -207,6 +213,8 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   }
   pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
   pp->cheb.js = js;
+  pp->cheb.probe_p = pp_;
+  pp->cheb.probe_seed = (uint32_t)o->probe_seed;
   if (pp->cheb.cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
   // slabs advance by the padded width: every unit column belongs to exactly one slab
   pp->width = pp->cheb.ldv;
@@ -279,7 +287,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   int nl = 0, nr = 0;
   double nb = 0.0;
   const double vec = (double)p.D * (double)p.ldv * (double)pp.elem;  // bytes of one slab vector
-  const int64_t ncols = p.D >> p.js;
+  const int64_t ncols = pass_columns(p);
   KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
@@ -665,6 +673,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
 
   if (opts && (opts->flags & KPM_FLAG_PH_HALF)) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by kpm_backward");
+  if (opts && opts->probe_p) return fail(ctx, KPM_EINVAL, "probing: not supported by kpm_backward");
   // slab width from the budget over all adjoint slab vectors (plus the forward pair);
   // the adjoint steps one moment per launch (its recomputed segments are stored)
   kpm_opts o = *opts;
@@ -775,6 +784,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
   }
   if ((r = check_dev(ctx, mu_eff, "mu_eff"))) return r;
   if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by the batched call");
+  if (opts->probe_p) return fail(ctx, KPM_EINVAL, "probing: not supported by the batched call");
   if (opts->M < 1 || (opts->precision != KPM_FP32 && opts->precision != KPM_FP64))
     return fail(ctx, KPM_EINVAL, "bad opts");
   DeviceGuard g(ctx->device);
@@ -1029,7 +1039,7 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int64_t D = 2 * (int64_t)N;
   const int prec = opts->precision;
   *best = *opts;
-  auto key = std::make_tuple(model->nx, model->ny, prec, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0);
+  auto key = std::make_tuple(model->nx, model->ny, prec, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0, opts->probe_p);
   auto hit = ctx->tuned.find(key);
   if (hit != ctx->tuned.end()) {
     best->block_width = std::get<0>(hit->second);
@@ -1044,7 +1054,9 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   KPM_CU(cudaEventCreate(&e0));
   KPM_CU(cudaEventCreate(&e1));
   // candidates: full width and narrower slabs (down to L2-resident ones), every column chunk
-  const int64_t ncols = (opts->flags & KPM_FLAG_PH_HALF) ? D / 2 : D;  // unit columns of a pass
+  // start vectors of a pass
+  const int64_t ncols = opts->probe_p > 0 ? std::min<int64_t>(D, 2 * (int64_t)opts->probe_p * opts->probe_p)
+                      : (opts->flags & KPM_FLAG_PH_HALF) ? D / 2 : D;
   std::vector<int64_t> widths = {ncols};
   for (int64_t w : {8192, 4096, 2048, 1024, 512, 384, 256, 128}) {
     const int64_t bw = balanced_width(ncols, w);

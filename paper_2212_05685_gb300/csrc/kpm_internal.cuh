@@ -30,7 +30,24 @@ struct ChebPlan {
   // slab column c holds unit vector J = (s0 + c) << js (js = 1: particle-hole
   // half pass over the columns (j, up) only; the pass covers D >> js columns)
   int js;
+  // probing (probe_p > 0): slab column c holds the probing vector of colour
+  // s0 + c (R = 2 probe_p^2 colours, phases from probe_seed)
+  int probe_p;
+  uint32_t probe_seed;
 };
+
+// What slab column c of a launch holds (built from the plan and the slab offset).
+struct ColMap {
+  int64_t s0;
+  int js;
+  int probe_p;
+  uint32_t seed;
+};
+inline ColMap colmap(const ChebPlan& p, int64_t s0) { return ColMap{s0, p.js, p.probe_p, p.probe_seed}; }
+// unit start vectors (D >> js) or probing vectors (2 p^2) of a pass
+inline int64_t pass_columns(const ChebPlan& p) {
+  return p.probe_p > 0 ? 2 * (int64_t)p.probe_p * p.probe_p : (p.D >> p.js);
+}
 
 // Per-cell pointers of a batch of equally shaped cells (FP32 recursion).
 constexpr int kMaxBatch = 64;

@@ -69,7 +69,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (!m || !o || !fields || !ab || !obs) return KPM_EINVAL;
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
-  if (o->flags & KPM_FLAG_PH_HALF) return KPM_EINVAL;  // the full pass only
+  if ((o->flags & KPM_FLAG_PH_HALF) || o->probe_p) return KPM_EINVAL;  // the exact full pass only
   if (!is_device(fields) || !is_device(ab) || !is_device(obs) || (omega && !is_device(omega))) return KPM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
