@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ph-half", action="store_true", help="skip the particle-hole half-pass section")
+    ap.add_argument("--no-probing", action="store_true", help="skip the probing-estimator section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
@@ -438,6 +439,8 @@ def run_ours(args):
                    "columns": f"{N} of {D} unit columns (j, up); the (j, dn) observables from the particle-hole relation",
                    "flags": oh.flags, "block_width": oh.block_width, "cols_per_block": oh.cols_per_block}
 
+    probe = None if args.no_probing else probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch)
+
     batched = None if args.no_batched else batched_section(kpm, inputs, torch)
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
     precision = precision_section(kpm, inputs, torch)
@@ -474,6 +477,7 @@ def run_ours(args):
         "fp64": fp64,
         "fp32_error": precision,
         "ph_half": ph_half,
+        "probing": probe,
         "batched": batched,
         "adjoint": adjoint,
         "residual_last": last.residual if last else None,
@@ -527,6 +531,49 @@ def batched_section(kpm, inputs, torch, iters=3):
     return {"cells": len(cells), "shapes": sorted({f"{w.nx}x{w.ny}" for w in cells}), "M": M, "precision": "fp32",
             "s_per_iteration": tb, "vector_moments_per_s": vm / tb,
             "sequential_s_per_iteration": ts, "sequential_vector_moments_per_s": vm / ts, "speedup": ts / tb}
+
+
+def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
+    """The paper's estimator (App. B): R = 2 p^2 coloured random-phase probing
+    vectors instead of all D unit vectors.  Per p: seconds per pass and per RMFT
+    iteration, and the largest error of each observable against the exact
+    (all-unit-vector) FP32 pass on the same Hamiltonian."""
+    N = model.nx * model.ny
+    D = 2 * N
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    exact = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_observables(ctx, model, kpm.make_opts(M, kpm.KPM_FP32), fields, ab, exact)
+    est = torch.empty_like(exact)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    rows = []
+    for p in (5, 10, 20, 25):
+        o = kpm.make_opts(M, kpm.KPM_FP32, probe_p=p, probe_seed=1)
+        kpm.kpm_observables(ctx, model, o, fields, ab, est)
+        torch.cuda.synchronize()
+        ev[0].record()
+        kpm.kpm_observables(ctx, model, o, fields, ab, est)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t_pass = ev[0].elapsed_time(ev[1]) / 1e3
+        d = (est - exact).abs()
+        # RMFT iterations with the estimator (fresh seed parameters)
+        pp = torch.tensor(p0, device="cuda")
+        mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+        kpm.rmft_iterate(ctx, model, o, ropts, phi, pp, mu, 1)
+        torch.cuda.synchronize()
+        ev[0].record()
+        kpm.rmft_iterate(ctx, model, o, ropts, phi, pp, mu, args.steps)
+        ev[1].record()
+        torch.cuda.synchronize()
+        rows.append({"p": p, "R": 2 * p * p, "s_per_pass": t_pass,
+                     "s_per_rmft_iteration": ev[0].elapsed_time(ev[1]) / 1e3 / args.steps,
+                     "max_err_n": float(d[:2 * N].max()), "max_err_chi": float(d[2 * N:18 * N].max()),
+                     "max_err_F": float(d[18 * N:].max())})
+    return {"estimator": "R = 2 p^2 probing vectors, colour alpha + 2((x mod p) + p (y mod p)), SplitMix64 phases",
+            "reference": f"exact FP32 pass over all {D} unit vectors", "M": M, "rows": rows}
 
 
 def precision_section(kpm, inputs, torch):

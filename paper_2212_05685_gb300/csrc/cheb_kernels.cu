@@ -105,23 +105,38 @@ __device__ __forceinline__ int probe_colour(int64_t K, int nx, int p) {
 
 // Moment-sum items of lattice row y for the chunk's columns [cb0, cb0 + CB):
 // unit vectors: item t = c * kSlots + s over the chunk's columns; probing:
-// t = r * kSlots + s over the 2 nx rows of lattice row y.  False when the item
-// has no source here; else the source row J, its chunk column c, the slot s
-// and the weight conj(xi_J) (1 for unit vectors).
-__device__ __forceinline__ int source_items(const ColMap& cm, int nx, int CB) {
-  return (cm.probe_p ? 2 * nx : CB) * kSlots;
+// the row's colours are 2 p (y mod p) + q, q = 2 (x mod p) + alpha in
+// [0, 2 p), so the chunk's colours that occur in the row form the range
+// [lo, lo + nq) and each has nx / p sources x = q / 2 + p k; item t =
+// ((k * nq) + qi) * kSlots + s.  source_item returns false when the item has
+// no source here; else the source row J, its chunk column c, the slot s and
+// the weight conj(xi_J) (1 for unit vectors).
+struct SourceRange {
+  int lo, nq;  // probing: first colour and number of the chunk's colours in the row
+};
+__device__ __forceinline__ int source_items(const ColMap& cm, int nx, int y, int64_t cb0, int CB, SourceRange& sr) {
+  if (!cm.probe_p) return CB * kSlots;
+  const int p = cm.probe_p;
+  const int64_t c0 = cm.s0 + cb0;
+  const int64_t base = 2 * (int64_t)p * (y % p);
+  const int64_t lo = c0 > base ? c0 : base;
+  const int64_t hi = min(c0 + CB, base + 2 * p);
+  sr.lo = (int)lo;
+  sr.nq = hi > lo ? (int)(hi - lo) : 0;
+  return sr.nq * (nx / p) * kSlots;
 }
-__device__ __forceinline__ bool source_item(const ColMap& cm, int t, int y, int nx, int64_t D, int64_t cb0, int CB,
-                                            int64_t& J, int& c, int& s, double2& wgt) {
+__device__ __forceinline__ bool source_item(const ColMap& cm, const SourceRange& sr, int t, int y, int nx, int64_t D,
+                                            int64_t cb0, int CB, int64_t& J, int& c, int& s, double2& wgt) {
   s = t % kSlots;
   const int r = t / kSlots;
   if (cm.probe_p) {
-    J = 2 * (int64_t)y * nx + r;
-    const int64_t col = probe_colour(J, nx, cm.probe_p) - cm.s0 - cb0;
-    if (col < 0 || col >= CB) return false;
-    c = (int)col;
-    const double2 xi = probe_xi(cm.seed, J);
-    wgt = make_double2(xi.x, -xi.y);
+    const int p = cm.probe_p;
+    const int qi = r % sr.nq, k = r / sr.nq;
+    const int colour = sr.lo + qi;
+    const int q = colour - 2 * p * (y % p);
+    J = 2 * ((int64_t)y * nx + (q >> 1) + p * k) + (q & 1);
+    c = (int)(colour - cm.s0 - cb0);
+    wgt = cm.xi[J];
     return true;
   }
   const int64_t col = cm.s0 + cb0 + r;
@@ -255,12 +270,13 @@ __global__ void __launch_bounds__(512, 1)
     if (MODE == 1 && acc != nullptr) {
       // moment sums of the columns whose own site lies in lattice row y
       const double cm = am[m], co = ao[m];
-      const int items = source_items(cmap, nx, CB);
+      SourceRange sr;
+      const int items = source_items(cmap, nx, y, cb0, CB, sr);
       for (int t = threadIdx.x; t < items; t += blockDim.x) {
         int64_t J;
         int c, s;
         double2 wgt;
-        if (!source_item(cmap, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
+        if (!source_item(cmap, sr, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
         const int64_t j = J >> 1;
         const int beta = (int)(J & 1);
         const int xs = wrapi((int)(j % nx) + kSlotDx[s], nx);
@@ -389,12 +405,13 @@ __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, 
                                             double2* __restrict__ acc) {
   constexpr int NV = CB / 2;
   constexpr int RS = 2 * NV;
-  const int items = source_items(cmap, nx, CB);
+  SourceRange sr;
+  const int items = source_items(cmap, nx, y, cb0, CB, sr);
   for (int t = threadIdx.x; t < items; t += blockDim.x) {
     int64_t J;
     int c, s;
     double2 wgt;
-    if (!source_item(cmap, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
+    if (!source_item(cmap, sr, t, y, nx, D, cb0, CB, J, c, s, wgt)) continue;
     const int64_t j = J >> 1;
     const int beta = (int)(J & 1);
     const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
@@ -745,7 +762,7 @@ __global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, i
     out = reinterpret_cast<float4*>(b.B[z]);
   }
   f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out,
-                          ColMap{0, 0, 0, 0u}, b.acc[z], b.am[z], b.ao[z], m);
+                          ColMap{0, 0, 0, 0u, nullptr}, b.acc[z], b.am[z], b.ao[z], m);
 }
 
 // V0: entry (K, c) of the start vector held by slab column c (unit vector
@@ -802,6 +819,13 @@ __global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int nx, ColMap cm, 
   }
 }
 
+__global__ void probe_phase_kernel(int64_t D, uint32_t seed, double2* __restrict__ xi_conj) {
+  for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < D; K += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = probe_xi(seed, K);
+    xi_conj[K] = make_double2(x.x, -x.y);
+  }
+}
+
 // acc += a_m V[local rows] (the last moment, which no step reads again)
 template <bool F32>
 __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const void* __restrict__ V,
@@ -817,8 +841,7 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
       J = r;
       c = probe_colour(J, nx, cm.probe_p) - cm.s0;
       if (c < 0 || c >= width) continue;
-      const double2 xi = probe_xi(cm.seed, J);
-      wgt = make_double2(xi.x, -xi.y);
+      wgt = cm.xi[J];
     } else {
       c = r;
       if (cm.s0 + c >= (D >> cm.js)) continue;
@@ -982,6 +1005,7 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.js = 0;
   p.probe_p = 0;
   p.probe_seed = 0;
+  p.xi = nullptr;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the
@@ -1107,6 +1131,12 @@ cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPt
     case 2: return launch_f32_batched<2>(p, ncell, b, m, mode, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((p.D + 255) / 256, 4 * kSMs));
+  probe_phase_kernel<<<grid, 256, 0, s>>>(p.D, p.probe_seed, xi_conj);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, int64_t s0, double2* acc,

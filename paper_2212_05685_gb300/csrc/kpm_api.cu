@@ -28,6 +28,8 @@ struct kpm_ctx {
   void* slab[4] = {nullptr, nullptr, nullptr, nullptr};  // two, or four for the double-step recursion
   int slab_n = 0;
   size_t slab_bytes = 0;
+  double2* xi = nullptr;  // probing phases conj(xi_J) of the current pass
+  size_t xi_bytes = 0;
   double2* acc = nullptr;
   size_t acc_bytes = 0;
   void* table = nullptr;
@@ -247,6 +249,10 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
   const size_t accb = (size_t)D * kSlots * sizeof(double2);
   if (ctx->acc_bytes < accb) drop_graph(ctx);
   if ((r = ensure(ctx, &ctx->acc, &ctx->acc_bytes, accb))) return r;
+  if (pp.cheb.probe_p > 0) {
+    if (ctx->xi_bytes < (size_t)D * sizeof(double2)) drop_graph(ctx);
+    if ((r = ensure(ctx, &ctx->xi, &ctx->xi_bytes, (size_t)D * sizeof(double2)))) return r;
+  }
   const size_t tb = (size_t)m->nx * m->ny * table_bytes_per_site(o->precision);
   if (ctx->table_bytes < tb) drop_graph(ctx);
   if ((r = ensure(ctx, &ctx->table, &ctx->table_bytes, tb))) return r;
@@ -281,7 +287,13 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
 int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
                  const double* ab, double* obs, double* omega, cudaStream_t s, bool events = false,
                  int* launches = nullptr, int* rec_launches = nullptr, double* rec_bytes = nullptr) {
-  const ChebPlan& p = pp.cheb;
+  ChebPlan p = pp.cheb;
+  int nl0 = 0;
+  if (p.probe_p > 0) {
+    p.xi = ctx->xi;
+    KPM_CU(launch_probe_phases(p, ctx->xi, s));
+    nl0 = 1;
+  }
   const int M = o->M;
   const int prec = o->precision;
   int nl = 0, nr = 0;
@@ -333,7 +345,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   }
   KPM_CU(launch_assemble(m->nx, m->ny, ctx->acc, ab, obs, omega, ctx->red, s, p.js));
   nl += omega ? 2 : 1;
-  if (launches) *launches = nl + nr;
+  if (launches) *launches = nl0 + nl + nr;
   if (rec_launches) *rec_launches = nr;
   if (rec_bytes) *rec_bytes = nb;
   return KPM_OK;
@@ -433,7 +445,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   drop_graph(ctx);
-  for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
+  for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->xi, (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
     if (p) cudaFree(p);

@@ -34,6 +34,7 @@ struct ChebPlan {
   // s0 + c (R = 2 probe_p^2 colours, phases from probe_seed)
   int probe_p;
   uint32_t probe_seed;
+  const double2* xi;  // device table conj(xi_J) of the pass (probing only)
 };
 
 // What slab column c of a launch holds (built from the plan and the slab offset).
@@ -42,8 +43,9 @@ struct ColMap {
   int js;
   int probe_p;
   uint32_t seed;
+  const double2* xi;  // conj(xi_J), J < D (probing)
 };
-inline ColMap colmap(const ChebPlan& p, int64_t s0) { return ColMap{s0, p.js, p.probe_p, p.probe_seed}; }
+inline ColMap colmap(const ChebPlan& p, int64_t s0) { return ColMap{s0, p.js, p.probe_p, p.probe_seed, p.xi}; }
 // unit start vectors (D >> js) or probing vectors (2 p^2) of a pass
 inline int64_t pass_columns(const ChebPlan& p) {
   return p.probe_p > 0 ? 2 * (int64_t)p.probe_p * p.probe_p : (p.D >> p.js);
@@ -114,6 +116,8 @@ cudaError_t launch_cheb_step2(const ChebPlan& p, const void* table, const void* 
 cudaError_t cheb_prepare_batched(const ChebPlan& p);
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
                                      cudaStream_t s);
+// table conj(xi_J) of the probing phases, J < D
+cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s);
 // acc += a_m V[local rows] for the slab's columns (no recursion)
 cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, int64_t s0,
                                double2* acc, const double* am, const double* ao, int m,
