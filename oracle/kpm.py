@@ -91,26 +91,50 @@ def cheb_eval(a, x):
     return out
 
 
-def coefficients(M, a, b):
-    """(a_m of the step, a^Omega_m of min(x-x0,0)) for bounds (a, b)."""
-    x0 = -b / a
-    return series(step_coeffs(M, x0), M), series(omega_coeffs(M, x0), M)
+def fermi(eps, T):
+    """Occupation 1 / (1 + e^{eps/T}) (T > 0)."""
+    return 0.5 * (1.0 - np.tanh(0.5 * np.asarray(eps, dtype=np.float64) / T))
+
+
+def grand(eps, T):
+    """Grand-potential function -T log(1 + e^{-eps/T}); min(eps, 0) as T -> 0."""
+    eps = np.asarray(eps, dtype=np.float64)
+    return -T * np.logaddexp(0.0, -eps / T)
+
+
+def coefficients(M, a, b, T=0.0, K=None):
+    """(a_m of the occupation, a^Omega_m of the grand-potential function) for
+    bounds (a, b): at T = 0 the step theta(x0 - x) and min(x - x0, 0) in closed
+    form (reading K3); at T > 0 (Eq. F_KPM with f = -T log(1 + e^{-(eps)/T}),
+    eps = a x + b) both by Chebyshev-Gauss quadrature with K = 4M nodes, the
+    route App. B names for C_m."""
+    if T <= 0.0:
+        x0 = -b / a
+        return series(step_coeffs(M, x0), M), series(omega_coeffs(M, x0), M)
+    K = 4 * M if K is None else K
+    c = chebyshev_gauss(lambda x: fermi(a * x + b, T), M, K)
+    co = chebyshev_gauss(lambda x: grand(a * x + b, T) / a, M, K)
+    return series(c, M), series(co, M)
 
 
 # ----------------------------------------------------------------------------- density matrices
 
-def f_ed(h):
-    """O0: exact T = 0 occupation U theta(-E) U^dagger (ties at E = 0 weigh 1/2)."""
+def f_ed(h, T=0.0):
+    """O0: exact occupation U f(E) U^dagger and Omega = sum_n g(E_n): at T = 0
+    the step (ties at E = 0 weigh 1/2) and min(E, 0); else Fermi and
+    -T log(1 + e^{-E/T})."""
     E, U = np.linalg.eigh(h)
+    if T > 0.0:
+        return (U * fermi(E, T)) @ U.conj().T, float(np.sum(grand(E, T)))
     occ = np.where(E < 0, 1.0, np.where(E > 0, 0.0, 0.5))
     return (U * occ) @ U.conj().T, float(np.sum(np.minimum(E, 0.0)))
 
 
-def f_spectral(h, a, b, M):
+def f_spectral(h, a, b, M, T=0.0):
     """O1: U F_M((E - b)/a) U^dagger and Omega_M = a tr G_M(h~)."""
     E, U = np.linalg.eigh(h)
     x = (E - b) / a
-    am, ao = coefficients(M, a, b)
+    am, ao = coefficients(M, a, b, T)
     Fx = cheb_eval(am, x)
     Gx = cheb_eval(ao, x)
     return (U * Fx) @ U.conj().T, float(a * np.sum(Gx))
