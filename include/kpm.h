@@ -75,6 +75,10 @@ typedef struct {
                            context's scratch budget (kpm_set_scratch_budget) */
   int32_t cols_per_block; /* columns per CTA in the recursion kernel; 0 = default */
   double margin;        /* spectral half-width margin of the Gershgorin rescale (0.01) */
+  double temperature;   /* 0: T = 0 step and min(eps, 0) in closed form; T > 0: Fermi
+                           function 1/(1 + e^{eps/T}) and grand-potential function
+                           -T log(1 + e^{-eps/T}) of the BdG energy eps, coefficients
+                           by Chebyshev-Gauss quadrature with 4 M nodes (App. B) */
   int32_t flags;        /* KPM_FLAG_* bits; 0 = defaults */
   int32_t probe_p;      /* 0: all unit start vectors (exact trace).  p >= 2, dividing nx
                            and ny: R = 2 p^2 probing vectors (App. B): Nambu row

@@ -60,11 +60,11 @@ def probing_matrix(nx, ny, p, seed):
     return Z, xi
 
 
-def f_probing(h, a, b, M, nx, ny, p, seed):
+def f_probing(h, a, b, M, nx, ny, p, seed, T=0.0):
     """(estimate of F_M(h~) column by column, estimate of Omega_M)."""
     E, U = np.linalg.eigh(h)
     x = (E - b) / a
-    am, ao = coefficients(M, a, b)
+    am, ao = coefficients(M, a, b, T)
     Z, xi = probing_matrix(nx, ny, p, seed)
     FZ = (U * cheb_eval(am, x)) @ (U.conj().T @ Z)
     Fest = FZ * np.conj(xi)[None, :]
@@ -73,6 +73,6 @@ def f_probing(h, a, b, M, nx, ny, p, seed):
     return Fest, omega
 
 
-def observables_probing(model, h, a, b, M, p, seed):
-    F, omega = f_probing(h, a, b, M, model.nx, model.ny, p, seed)
+def observables_probing(model, h, a, b, M, p, seed, T=0.0):
+    F, omega = f_probing(h, a, b, M, model.nx, model.ny, p, seed, T)
     return observables(model, F), omega

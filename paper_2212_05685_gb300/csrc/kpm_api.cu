@@ -199,6 +199,7 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
+  if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return fail(ctx, KPM_EINVAL, "temperature must be finite and >= 0");
   const int pp_ = o->probe_p;
   if (pp_ < 0 || pp_ == 1 || (pp_ > 0 && (m->nx % pp_ != 0 || m->ny % pp_ != 0)))
     return fail(ctx, KPM_EINVAL, "probe_p must be 0 or >= 2 and divide nx and ny");
@@ -300,7 +301,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   double nb = 0.0;
   const double vec = (double)p.D * (double)p.ldv * (double)pp.elem;  // bytes of one slab vector
   const int64_t ncols = pass_columns(p);
-  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js));
+  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js, o->temperature));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
   else
@@ -716,7 +717,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int prec = o.precision;
   void* A = ctx->slab[0];
   void* B = ctx->slab[1];
-  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s));
+  KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, 0, o.temperature));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*model, fields, ab, (float2*)ctx->table, s));
   else
@@ -941,7 +942,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       KPM_TRY(launch_fields(m, phis[c], params[c], 0.0, C.fields, nullptr, c0));
       KPM_TRY(launch_shift_eps(N, C.fields, mu_eff + c, C.misc + 6, C.misc + 2, ctx->bred, c0));
       KPM_TRY(launch_gershgorin(m, C.fields, opts->margin, C.misc, ctx->bred, c0));
-      KPM_TRY(launch_coefficients(M, C.misc, C.am, C.ao, c0));
+      KPM_TRY(launch_coefficients(M, C.misc, C.am, C.ao, c0, 0, opts->temperature));
       if (prec == KPM_FP32)
         KPM_TRY(launch_scale_table_f32(m, C.fields, C.misc, (float2*)C.table, c0));
       else

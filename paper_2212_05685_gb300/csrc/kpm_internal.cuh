@@ -75,8 +75,10 @@ cudaError_t launch_gershgorin(const kpm_model& m, const double* fields, double m
                               double* red, cudaStream_t s, int symmetric = 0);
 // out2 = {max deviation from eps_up = eps_dn, T_up = T_dn, D_ij = D_ji; max field modulus}
 cudaError_t launch_ph_asym(const kpm_model& m, const double* fields, double* out2, double* red, cudaStream_t s);
-// a_m (step) and a^Omega_m coefficients from device (a, b); half: a^Omega_m (1 + (-1)^m)
-cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half = 0);
+// a_m (occupation) and a^Omega_m (grand potential) coefficients from device (a, b) at
+// temperature T (0: closed-form step); half: a^Omega_m (1 + (-1)^m)
+cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half = 0,
+                                double temperature = 0.0);
 // per-site table of 2h~ entries in precision T (kCoef complex per site)
 cudaError_t launch_scale_table_f32(const kpm_model& m, const double* fields, const double* ab,
                                    float2* table, cudaStream_t s);

@@ -70,6 +70,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
   if ((o->flags & KPM_FLAG_PH_HALF) || o->probe_p) return KPM_EINVAL;  // the exact full pass only
+  if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return KPM_EINVAL;
   if (!is_device(fields) || !is_device(ab) || !is_device(obs) || (omega && !is_device(omega))) return KPM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -129,7 +130,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
     }                                \
   } while (0)
   KPM_NA(cheb_prepare(p, prec));
-  KPM_NA(launch_coefficients(M, ab, am, ao, s));
+  KPM_NA(launch_coefficients(M, ab, am, ao, s, 0, o->temperature));
   if (prec == KPM_FP32)
     KPM_NA(launch_scale_table_f32(*m, fields, ab, (float2*)table, s));
   else

@@ -703,8 +703,46 @@ cudaError_t launch_ph_asym(const kpm_model& m, const double* fields, double* out
   return cudaGetLastError();
 }
 
-cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half) {
-  coefficients_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, ab, am, ao, half);
+// T > 0: c_m = (1/K) sum_k f(x_k) cos(m th_k), th_k = pi (k + 1/2)/K, x_k =
+// cos th_k, K = 4 M (Chebyshev-Gauss quadrature, App. B) for the Fermi
+// function f of eps = a x + b and for G = g(eps)/a, g(eps) = -T log(1 + e^{-eps/T});
+// one block per m, the cosine argument reduced exactly as m (2k+1) mod 4K.
+__global__ void coefficients_T_kernel(int M, const double* __restrict__ ab, double T, double* __restrict__ am,
+                                      double* __restrict__ ao, int half) {
+  const int m = blockIdx.x;
+  const double a = ab[0], b = ab[1];
+  const int64_t K = 4 * (int64_t)M;
+  double sf = 0.0, sg = 0.0;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+    const double x = cospi((double)(2 * k + 1) / (double)(2 * K));
+    const double e = a * x + b;
+    const double f = 0.5 * (1.0 - tanh(0.5 * e / T));
+    const double z = -e / T;  // softplus(z) = log(1 + e^z), evaluated without overflow
+    const double sp = z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+    const double g = -T * sp / a;
+    const int64_t n = ((int64_t)m * (2 * k + 1)) % (4 * K);
+    const double c = cospi((double)n / (double)(2 * K));
+    sf += f * c;
+    sg += g * c;
+  }
+  sf = block_reduce<0>(sf);
+  sg = block_reduce<0>(sg);
+  if (threadIdx.x == 0) {
+    const double q = kPi / (M + 1);
+    const double gm = ((M - m + 1) * cos(q * m) + sin(q * m) * cos(q) / sin(q)) / (M + 1);
+    const double w = m == 0 ? 1.0 : 2.0;
+    am[m] = w * gm * sf / (double)K;
+    const double o = w * gm * sg / (double)K;
+    ao[m] = half ? ((m & 1) ? 0.0 : 2.0 * o) : o;
+  }
+}
+
+cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half,
+                                double temperature) {
+  if (temperature > 0.0)
+    coefficients_T_kernel<<<M, kRedBlock, 0, s>>>(M, ab, temperature, am, ao, half);
+  else
+    coefficients_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, ab, am, ao, half);
   return cudaGetLastError();
 }
 

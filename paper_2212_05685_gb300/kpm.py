@@ -35,7 +35,8 @@ class kpm_model(ctypes.Structure):
 
 class kpm_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("precision", ctypes.c_int32), ("block_width", ctypes.c_int32),
-                ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double), ("flags", ctypes.c_int32),
+                ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("flags", ctypes.c_int32),
                 ("probe_p", ctypes.c_int32), ("probe_seed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -133,8 +134,8 @@ def make_model(nx, ny, t=1.0, tp=-0.3, J=0.3, flux=1, gutzwiller=True):
 
 
 def make_opts(M, precision=KPM_FP32, block_width=0, cols_per_block=0, margin=0.01, flags=0, probe_p=0,
-              probe_seed=0):
-    return kpm_opts(M, precision, block_width, cols_per_block, margin, flags, probe_p, probe_seed, 0)
+              probe_seed=0, temperature=0.0):
+    return kpm_opts(M, precision, block_width, cols_per_block, margin, temperature, flags, probe_p, probe_seed, 0)
 
 
 def make_rmft_opts(n_target, alpha=0.5, alpha_n=0.05, eta=0.5, tol=1e-7, paramagnetic=True):
