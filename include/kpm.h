@@ -254,6 +254,26 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
 int kpm_observables_noalloc(const kpm_model* model, const kpm_opts* opts, const double* fields,
                             const double* ab, double* obs, double* omega, void* stream);
 
+/* Local density of states (App. C, Eqs. N_i and Gij):
+ *   N_i,up(w) = -(g^t_i,up)^2 Im G_(i,up)(w + i Gamma) / pi,
+ *   N_i,dn(w) = -(g^t_i,dn)^2 Im G_(i,dn)(-w + i Gamma) / pi,
+ *   Gamma = gamma_alpha |w| + gamma0   (the paper: 0.25 |w| + 3e-4),
+ * with G_II(z) = [(z - h)^-1]_II evaluated as the Chebyshev series of the
+ * resolvent truncated at opts->M terms: (1/a)(1/s) sum_m (2 - delta_m0) w^m
+ * [T_m(h~)]_II, z~ = (z - b)/a, s = sqrt(z~^2 - 1), w = z~ - s, |w| < 1.  The
+ * series converges like |w|^M, i.e. it needs M well above a / Gamma near the
+ * spectrum.  The diagonal moments come from one recursion pass (all unit
+ * vectors, or their probing estimate when opts->probe_p > 0); the sum over
+ * m is one FP64 GEMM per spin (cuBLAS).  params: device, 26 N, for the
+ * Gutzwiller weights (g^t_i,sigma)^2 (reading L1), or NULL for weights 1.
+ * omega: host or device array of n_omega frequencies (units of t, energy 0 =
+ * the chemical potential inside h).  ldos: device, [2][n_omega][N] (spin up,
+ * spin down).  Scratch: M x 2N + 2 n_omega M doubles.  Not with
+ * KPM_FLAG_PH_HALF (KPM_EINVAL); gamma0 must be > 0. */
+int kpm_ldos(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields, const double* ab,
+             const double* params, int n_omega, const double* omega, double gamma_alpha, double gamma0, double* ldos,
+             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

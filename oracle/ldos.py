@@ -66,14 +66,10 @@ def resolvent_coeffs(z, M):
     return c
 
 
-def ldos_cheb(h, a, b, M, omega, alpha=0.25, gamma0=3e-4, weights=None):
-    E, U = np.linalg.eigh(h)
-    x = (E - b) / a
-    D = h.shape[0]
+def ldos_from_moments(mu, a, b, omega, alpha=0.25, gamma0=3e-4, weights=None):
+    """LDOS [2][n_omega][N] from diagonal moments mu[m][I] (M x D)."""
+    M, D = mu.shape
     N = D // 2
-    # diagonal moments mu[m][I] = sum_n |U_In|^2 T_m(x_n)
-    T = np.cos(np.arange(M)[:, None] * np.arccos(np.clip(x, -1.0, 1.0))[None, :])
-    mu = T @ (np.abs(U) ** 2).T              # (M, D)
     out = np.empty((2, len(omega), N))
     for s in range(2):
         sign = 1.0 if s == 0 else -1.0
@@ -84,4 +80,29 @@ def ldos_cheb(h, a, b, M, omega, alpha=0.25, gamma0=3e-4, weights=None):
             out[s, k] = -G.imag / np.pi
     if weights is not None:
         out *= weights[:, None, :]
-    return out, mu
+    return out
+
+
+def moments(h, a, b, M):
+    """Diagonal moments [T_m(h~)]_II from the eigenpairs (M x D)."""
+    E, U = np.linalg.eigh(h)
+    x = (E - b) / a
+    T = np.cos(np.arange(M)[:, None] * np.arccos(np.clip(x, -1.0, 1.0))[None, :])
+    return T @ (np.abs(U) ** 2).T
+
+
+def moments_probing(h, a, b, M, nx, ny, p, seed):
+    """Probing estimate Re(conj(xi_J) [T_m(h~) r_colour(J)]_J) of the diagonal moments."""
+    from .probing import probing_matrix
+    E, U = np.linalg.eigh(h)
+    x = (E - b) / a
+    T = np.cos(np.arange(M)[:, None] * np.arccos(np.clip(x, -1.0, 1.0))[None, :])
+    Z, xi = probing_matrix(nx, ny, p, seed)
+    W = U.conj().T @ Z                        # (n, J)
+    P = U.T * W                               # P[n, J] = U[J, n] W[n, J]
+    return ((T @ P) * np.conj(xi)[None, :]).real
+
+
+def ldos_cheb(h, a, b, M, omega, alpha=0.25, gamma0=3e-4, weights=None):
+    mu = moments(h, a, b, M)
+    return ldos_from_moments(mu, a, b, omega, alpha, gamma0, weights), mu

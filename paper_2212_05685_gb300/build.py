@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libkpm.so")
-SOURCES = ["cheb_kernels.cu", "rmft_kernels.cu", "kpm_api.cu", "kpm_noalloc.cu", "kpm_adjoint.cu"]
+SOURCES = ["cheb_kernels.cu", "rmft_kernels.cu", "kpm_api.cu", "kpm_noalloc.cu", "kpm_adjoint.cu", "kpm_ldos.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -49,7 +49,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-lcublas", "-o", tmp]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

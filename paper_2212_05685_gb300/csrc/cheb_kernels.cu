@@ -151,6 +151,11 @@ __device__ __forceinline__ void acc_add(double2* a, double coef, double2 w, doub
   a->x += coef * (w.x * vr - w.y * vi);
   a->y += coef * (w.x * vi + w.y * vr);
 }
+// diagonal moment [T_m(h~)]_JJ (its estimate for probing) into the record
+__device__ __forceinline__ void record_diag(const ColMap& cm, int64_t D, int m, int64_t J, double2 w, double vr,
+                                            double vi) {
+  cm.rec[(int64_t)m * D + (J & 1) * (D >> 1) + (J >> 1)] = w.x * vr - w.y * vi;
+}
 
 // one lattice row of V (2 nx Nambu rows x CB columns) into shared memory
 template <typename C, int CB>
@@ -285,6 +290,7 @@ __global__ void __launch_bounds__(512, 1)
         const int al = kSlotFlip[s] ? 1 - beta : beta;
         const C val = w[(2 * xs + al) * CB + c];
         acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
+        if (s == 0 && cmap.rec) record_diag(cmap, D, m, J, wgt, (double)val.x, (double)val.y);
       }
     }
     __syncthreads();
@@ -401,7 +407,7 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
 // own site lies in lattice row y; wm, w0, wp hold rows y-1, y, y+1
 template <int CB, bool SW = false>
 __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, const float4* wp, int nx, int y,
-                                            int64_t D, const ColMap& cmap, int64_t cb0, double cm, double co,
+                                            int64_t D, const ColMap& cmap, int64_t cb0, int m, double cm, double co,
                                             double2* __restrict__ acc) {
   constexpr int NV = CB / 2;
   constexpr int RS = 2 * NV;
@@ -420,6 +426,7 @@ __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, 
     const int al = kSlotFlip[s] ? 1 - beta : beta;
     const float2 val = pair_elem(w + xsl * RS + nambu_slot<NV, SW>(xsl, al) * NV, c);
     acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
+    if (s == 0 && cmap.rec) record_diag(cmap, D, m, J, wgt, (double)val.x, (double)val.y);
   }
 }
 
@@ -552,7 +559,7 @@ __device__ __forceinline__ void f32_step_body(int nx, int ny, int64_t D, int64_t
     }
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
-      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, am[m], ao[m], acc);
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, m, am[m], ao[m], acc);
     bm = b0;
     bc = bc + 1 == 3 ? 0 : bc + 1;
     if (MODE == 1) {
@@ -703,7 +710,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         }
       }
       if (acc != nullptr && f >= y0 && f < y1 && f >= yj_lo && f <= yj_hi)
-        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, cmap, cb0, am[m], ao[m], acc);
+        moment_sums<CB, SW>(wm - v, w0 - v, wp - v, nx, f, D, cmap, cb0, m, am[m], ao[m], acc);
     }
     __syncthreads();
 
@@ -730,7 +737,7 @@ __device__ __forceinline__ void f32_step2_body(int nx, int ny, int64_t D, int64_
         *reinterpret_cast<ulonglong2*>(gp + ldq) = o1;
       }
       if (acc != nullptr && g >= yj_lo && g <= yj_hi)
-        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, cmap, cb0, am[m + 1], ao[m + 1], acc);
+        moment_sums<CB, SW>(rm - v, r0 - v, rf - v, nx, g, D, cmap, cb0, m + 1, am[m + 1], ao[m + 1], acc);
     }
     pc[0][0] = pn[0][0];
     pc[0][1] = pn[0][1];
@@ -762,7 +769,7 @@ __global__ void __launch_bounds__(512, 1) cheb_step_f32_batched_kernel(int nx, i
     out = reinterpret_cast<float4*>(b.B[z]);
   }
   f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, reinterpret_cast<const float2*>(b.table[z]), cur, out, out,
-                          ColMap{0, 0, 0, 0u, nullptr}, b.acc[z], b.am[z], b.ao[z], m);
+                          ColMap{0, 0, 0, 0u, nullptr, nullptr}, b.acc[z], b.am[z], b.ao[z], m);
 }
 
 // V0: entry (K, c) of the start vector held by slab column c (unit vector
@@ -816,6 +823,7 @@ __global__ void cheb_init_acc_kernel(int64_t D, int64_t ldv, int nx, ColMap cm, 
     if (s == 0) a.x = am[0];
     if (s == kSlots - 1) a.x = ao[0];
     acc[J * kSlots + s] = a;
+    if (s == 0 && cm.rec) cm.rec[(J & 1) * (D >> 1) + (J >> 1)] = 1.0;  // T_0 = 1
   }
 }
 
@@ -864,6 +872,7 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
       im = val.y;
     }
     acc_add(acc + J * kSlots + s, s == kSlots - 1 ? ao[m] : am[m], wgt, re, im);
+    if (s == 0 && cm.rec) record_diag(cm, D, m, J, wgt, re, im);
   }
 }
 
@@ -1006,6 +1015,7 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   p.probe_p = 0;
   p.probe_seed = 0;
   p.xi = nullptr;
+  p.rec = nullptr;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
   // enough CTAs to fill the GPU a few times over: split y only when the

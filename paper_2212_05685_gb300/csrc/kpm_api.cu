@@ -30,6 +30,10 @@ struct kpm_ctx {
   size_t slab_bytes = 0;
   double2* xi = nullptr;  // probing phases conj(xi_J) of the current pass
   size_t xi_bytes = 0;
+  // LDOS: diagonal-moment record, coefficient matrix, weights, frequencies, cuBLAS handle
+  double* ldos_buf = nullptr;
+  size_t ldos_buf_bytes = 0;
+  void* cublas = nullptr;
   double2* acc = nullptr;
   size_t acc_bytes = 0;
   void* table = nullptr;
@@ -287,8 +291,10 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
 // the last slab); *launches / *rec_launches count the kernels enqueued.
 int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
                  const double* ab, double* obs, double* omega, cudaStream_t s, bool events = false,
-                 int* launches = nullptr, int* rec_launches = nullptr, double* rec_bytes = nullptr) {
+                 int* launches = nullptr, int* rec_launches = nullptr, double* rec_bytes = nullptr,
+                 double* diag_record = nullptr) {
   ChebPlan p = pp.cheb;
+  p.rec = diag_record;
   int nl0 = 0;
   if (p.probe_p > 0) {
     p.xi = ctx->xi;
@@ -446,7 +452,9 @@ int kpm_destroy(kpm_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   drop_graph(ctx);
-  for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->xi, (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
+  cublas_destroy(ctx->cublas);
+  for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->xi, (void*)ctx->ldos_buf,
+                  (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
     if (p) cudaFree(p);
@@ -779,6 +787,49 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   KPM_CU(launch_grad_reduce(D, groups, Gpart, ctx->Gacc, s));
   KPM_CU(launch_grad_fields(model->nx, model->ny, ctx->Gacc, ab, grad_fields, s));
   if (grad_phi) KPM_CU(launch_phi_grad(*model, phi, params, grad_fields, grad_phi, s));
+  return KPM_OK;
+}
+
+int kpm_ldos(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields, const double* ab,
+             const double* params, int n_omega, const double* omega, double gamma_alpha, double gamma0, double* ldos,
+             void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, fields, "fields")) || (r = check_dev(ctx, ab, "ab")) || (r = check_dev(ctx, ldos, "ldos")))
+    return r;
+  if (params && (r = check_dev(ctx, params, "params"))) return r;
+  if (!opts || !omega || n_omega < 1) return fail(ctx, KPM_EINVAL, "bad LDOS arguments");
+  if (!(gamma0 > 0.0) || !(gamma_alpha >= 0.0)) return fail(ctx, KPM_EINVAL, "need gamma0 > 0 and gamma_alpha >= 0");
+  if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: the LDOS needs both Nambu rows");
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  const int64_t D = 2 * (int64_t)N;
+  const int M = opts->M;
+  kpm_opts o = *opts;
+  o.flags &= ~KPM_FLAG_DOUBLE_STEP;  // one step per launch
+  if ((r = ensure_site_scratch(ctx, N))) return r;
+  PassPlan pp;
+  if ((r = plan_pass(ctx, model, &o, &pp))) return r;
+  if ((r = ensure_pass_scratch(ctx, model, &o, pp))) return r;
+  // scratch: record M x D, coefficients 2 x n_omega x M, weights 2N, frequencies n_omega
+  const size_t rec_n = (size_t)M * D, c_n = 2 * (size_t)n_omega * M;
+  const size_t need = (rec_n + c_n + 2 * (size_t)N + (size_t)n_omega) * sizeof(double);
+  if ((r = ensure(ctx, &ctx->ldos_buf, &ctx->ldos_buf_bytes, need))) return r;
+  double* rec = ctx->ldos_buf;
+  double* C = rec + rec_n;
+  double* wgt = C + c_n;
+  double* om = wgt + 2 * (size_t)N;
+  if (!ctx->cublas && !(ctx->cublas = cublas_create())) return fail(ctx, KPM_ECUDA, "cublasCreate failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  KPM_CU(cudaMemcpyAsync(om, omega, n_omega * sizeof(double),
+                         is_device_ptr(omega) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s, false, nullptr, nullptr, nullptr, rec)))
+    return r;
+  if (params) KPM_CU(launch_gt_weights(*model, params, wgt, s));
+  KPM_CU(launch_ldos_coefficients(M, n_omega, om, gamma_alpha, gamma0, ab, C, s));
+  const char* err = ldos_contract(ctx->cublas, M, n_omega, N, C, rec, ldos, params ? wgt : nullptr, s);
+  if (err) return fail(ctx, KPM_ECUDA, err);
   return KPM_OK;
 }
 

@@ -35,6 +35,7 @@ struct ChebPlan {
   int probe_p;
   uint32_t probe_seed;
   const double2* xi;  // device table conj(xi_J) of the pass (probing only)
+  double* rec;        // diagonal moments [T_m(h~)]_JJ, rec[m D + (J & 1) N + (J >> 1)] (or null)
 };
 
 // What slab column c of a launch holds (built from the plan and the slab offset).
@@ -44,8 +45,9 @@ struct ColMap {
   int probe_p;
   uint32_t seed;
   const double2* xi;  // conj(xi_J), J < D (probing)
+  double* rec;        // diagonal-moment record (or null)
 };
-inline ColMap colmap(const ChebPlan& p, int64_t s0) { return ColMap{s0, p.js, p.probe_p, p.probe_seed, p.xi}; }
+inline ColMap colmap(const ChebPlan& p, int64_t s0) { return ColMap{s0, p.js, p.probe_p, p.probe_seed, p.xi, p.rec}; }
 // unit start vectors (D >> js) or probing vectors (2 p^2) of a pass
 inline int64_t pass_columns(const ChebPlan& p) {
   return p.probe_p > 0 ? 2 * (int64_t)p.probe_p * p.probe_p : (p.D >> p.js);
@@ -144,5 +146,17 @@ cudaError_t launch_grad_fields(int nx, int ny, const double2* G, const double* a
 // dL/dphi through the fields' dependence on the Peierls phases (rmft_kernels.cu)
 cudaError_t launch_phi_grad(const kpm_model& m, const double* phi, const double* params, const double* grad_fields,
                             double* grad_phi, cudaStream_t s);
+
+// ---------------------------------------------------------------- kpm_ldos.cu
+// C[sigma][k][m] of the resolvent series (see kpm_ldos.cu)
+cudaError_t launch_ldos_coefficients(int M, int nw, const double* omega, double alpha, double gamma0,
+                                     const double* ab, double* C, cudaStream_t s);
+// ldos = -w/pi * (moments x coefficients), one FP64 GEMM per spin; null or an error message
+const char* ldos_contract(void* cublas, int M, int nw, int64_t N, const double* C, const double* rec, double* ldos,
+                          const double* wgt, cudaStream_t s);
+void* cublas_create();
+void cublas_destroy(void* h);
+// (g^t_{i sigma})^2 per site and spin, [2][N] (rmft_kernels.cu)
+cudaError_t launch_gt_weights(const kpm_model& m, const double* params, double* w, cudaStream_t s);
 
 }  // namespace kpm

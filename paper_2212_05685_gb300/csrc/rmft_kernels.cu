@@ -737,6 +737,22 @@ __global__ void coefficients_T_kernel(int M, const double* __restrict__ ab, doub
   }
 }
 
+__global__ void gt_weights_kernel(kpm_model m, const double* __restrict__ params, double* __restrict__ w) {
+  const int N = m.nx * m.ny;
+  const Layout L{N};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const SiteF f = site_factors(L.n(params, 0, i), L.n(params, 1, i), m.gutzwiller != 0);
+  w[i] = f.gt[0] * f.gt[0];
+  w[N + i] = f.gt[1] * f.gt[1];
+}
+
+cudaError_t launch_gt_weights(const kpm_model& m, const double* params, double* w, cudaStream_t s) {
+  const int N = m.nx * m.ny;
+  gt_weights_kernel<<<(N + 127) / 128, 128, 0, s>>>(m, params, w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao, cudaStream_t s, int half,
                                 double temperature) {
   if (temperature > 0.0)

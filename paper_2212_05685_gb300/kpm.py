@@ -68,6 +68,8 @@ _SIGNATURES = {
     "rmft_iterate": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts),
                                     ctypes.POINTER(kpm_rmft_opts), _P, _P, _P, ctypes.c_int,
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
+    "kpm_ldos": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P, ctypes.c_int,
+                                _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
                                                _P, _P]),
     "kpm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P,
@@ -258,3 +260,14 @@ def kpm_observables_noalloc(model, opts, fields, ab, obs, omega=None, stream=Non
     lib = load()
     return lib.kpm_observables_noalloc(ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
                                        _ptr(obs), _ptr(omega), _stream(stream))
+
+
+def kpm_ldos(ctx: Context, model, opts, fields, ab, params, omega, ldos, gamma_alpha=0.25, gamma0=3e-4, stream=None):
+    """Local density of states [2][len(omega)][N] into `ldos` (device); omega a
+    float64 numpy array or CUDA tensor; params a CUDA tensor or None."""
+    import numpy as np
+    if not hasattr(omega, "data_ptr"):
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+    return ctx.check(ctx.lib.kpm_ldos(ctx.handle, ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
+                                      _ptr(params), int(len(omega)), _ptr(omega), float(gamma_alpha), float(gamma0),
+                                      _ptr(ldos), _stream(stream)), "kpm_ldos")
