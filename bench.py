@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ph-half", action="store_true", help="skip the particle-hole half-pass section")
     ap.add_argument("--no-probing", action="store_true", help="skip the probing-estimator section")
+    ap.add_argument("--no-ldos", action="store_true", help="skip the LDOS section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
@@ -440,6 +441,7 @@ def run_ours(args):
                    "flags": oh.flags, "block_width": oh.block_width, "cols_per_block": oh.cols_per_block}
 
     probe = None if args.no_probing else probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch)
+    ldos_res = None if args.no_ldos else ldos_section(kpm, ctx, model, phi, torch.tensor(p0, device="cuda"), torch)
 
     batched = None if args.no_batched else batched_section(kpm, inputs, torch)
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
@@ -478,6 +480,7 @@ def run_ours(args):
         "fp32_error": precision,
         "ph_half": ph_half,
         "probing": probe,
+        "ldos": ldos_res,
         "batched": batched,
         "adjoint": adjoint,
         "residual_last": last.residual if last else None,
@@ -574,6 +577,40 @@ def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
                      "max_err_F": float(d[18 * N:].max())})
     return {"estimator": "R = 2 p^2 probing vectors, colour alpha + 2((x mod p) + p (y mod p)), SplitMix64 phases",
             "reference": f"exact FP32 pass over all {D} unit vectors", "M": M, "rows": rows}
+
+
+def ldos_section(kpm, ctx, model, phi, params, torch):
+    """LDOS of the 100x100 cell at the seed parameters (App. C): 201
+    frequencies in [-0.5 t, 0.5 t], Gamma = 0.25 |w| + 3e-4 t, Gutzwiller
+    weights; diagonal moments by probing (p = 10, R = 200) at M = 65536 (the
+    resolvent series converges like |w|^M, |w| ~ 1 - Gamma/a at the band
+    centre, so M must exceed a few a / Gamma_0)."""
+    import numpy as np
+    N = model.nx * model.ny
+    M, p, nw = 65536, 10, 201
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    omega = np.linspace(-0.5, 0.5, nw)
+    out = torch.empty(2 * nw * N, dtype=torch.float64, device="cuda")
+    opts = kpm.make_opts(M, kpm.KPM_FP32, probe_p=p, probe_seed=1)
+    kpm.kpm_ldos(ctx, model, opts, fields, ab, params, omega, out)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    kpm.kpm_ldos(ctx, model, opts, fields, ab, params, omega, out)
+    ev[1].record()
+    torch.cuda.synchronize()
+    a = float(ab[0])
+    # truncation |w|^M at the band centre, w = z - sqrt(z^2 - 1), z = i Gamma_0 / a
+    z = 1j * 3e-4 / a
+    wc = abs(z - np.sqrt(z * z - 1))
+    tot = out.view(2, nw, N).sum(0)
+    return {"cell": "100x100", "n_omega": nw, "omega_range_t": [-0.5, 0.5], "gamma": "0.25|w| + 3e-4",
+            "M": M, "moments": f"probing p={p} (R={2 * p * p})", "precision": "fp32 recursion, fp64 moments and GEMM",
+            "s_total": ev[0].elapsed_time(ev[1]) / 1e3, "truncation_at_w0": wc ** M,
+            "mean_ldos_at_w0": float(tot[nw // 2].mean())}
 
 
 def precision_section(kpm, inputs, torch):
