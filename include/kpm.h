@@ -254,6 +254,17 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
 int kpm_observables_noalloc(const kpm_model* model, const kpm_opts* opts, const double* fields,
                             const double* ab, double* obs, double* omega, void* stream);
 
+/* Vortex-profile order parameters (Sec. III, Eqs. giDelta and gm):
+ *   Delta_i = 1/8 sum_{sigma, tau = +-x, +-y} g^t_i,sigma g^t_{i+tau},sigma (-1)^{tau_y}
+ *             Delta_{i,i+tau,sigma} e^{i phi_{i,i+tau}},
+ *   Delta_{ij,up} = F_ij, Delta_{ij,dn} = F_ji, the bond phase sign chosen so that
+ *   Delta_i transforms like a pair at site i under gauge changes;
+ *   M_i = (-1)^{x+y} g^{s,xy}_i / 4 sum_tau sqrt(g^{s,z}_{i,i+tau} / g^{s,xy}_{i,i+tau}) m_i.
+ * phi (4N), params (26N): device.  delta_out: device, 2N doubles (re, im per
+ * site); mag_out: device, N doubles. */
+int kpm_order_parameters(kpm_ctx* ctx, const kpm_model* model, const double* phi, const double* params,
+                         double* delta_out, double* mag_out, void* stream);
+
 /* Local density of states (App. C, Eqs. N_i and Gij):
  *   N_i,up(w) = -(g^t_i,up)^2 Im G_(i,up)(w + i Gamma) / pi,
  *   N_i,dn(w) = -(g^t_i,dn)^2 Im G_(i,dn)(-w + i Gamma) / pi,

@@ -790,6 +790,19 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   return KPM_OK;
 }
 
+int kpm_order_parameters(kpm_ctx* ctx, const kpm_model* model, const double* phi, const double* params,
+                         double* delta_out, double* mag_out, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if ((r = check_dev(ctx, phi, "phi")) || (r = check_dev(ctx, params, "params")) ||
+      (r = check_dev(ctx, delta_out, "delta_out")) || (r = check_dev(ctx, mag_out, "mag_out")))
+    return r;
+  DeviceGuard g(ctx->device);
+  KPM_CU(launch_order_parameters(*model, phi, params, delta_out, mag_out, (cudaStream_t)stream));
+  return KPM_OK;
+}
+
 int kpm_ldos(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields, const double* ab,
              const double* params, int n_omega, const double* omega, double gamma_alpha, double gamma0, double* ldos,
              void* stream) {

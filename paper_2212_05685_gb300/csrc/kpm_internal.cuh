@@ -156,6 +156,9 @@ const char* ldos_contract(void* cublas, int M, int nw, int64_t N, const double* 
                           const double* wgt, cudaStream_t s);
 void* cublas_create();
 void cublas_destroy(void* h);
+// physical pairing Delta_i (2N: re, im) and staggered magnetisation M_i (N) (rmft_kernels.cu)
+cudaError_t launch_order_parameters(const kpm_model& m, const double* phi, const double* params, double* delta_out,
+                                    double* mag_out, cudaStream_t s);
 // (g^t_{i sigma})^2 per site and spin, [2][N] (rmft_kernels.cu)
 cudaError_t launch_gt_weights(const kpm_model& m, const double* params, double* w, cudaStream_t s);
 

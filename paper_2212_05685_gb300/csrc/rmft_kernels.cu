@@ -737,6 +737,52 @@ __global__ void coefficients_T_kernel(int M, const double* __restrict__ ab, doub
   }
 }
 
+// Vortex-profile order parameters (Eqs. giDelta, gm): the physical pairing
+// Delta_i = 1/8 sum_{sigma,tau} g^t_i,sigma g^t_{i+tau},sigma (-1)^{tau_y}
+// Delta_{i,i+tau,sigma} e^{i phi_{i,i+tau}} (Delta_up = F_ij, Delta_dn = F_ji; the
+// bond phase sign makes Delta_i a pair at site i under gauge changes) and
+// M_i = (-1)^{x+y} g^xy_i/4 sum_tau sqrt(R_{i,i+tau}) m_i (R = g^z/g^xy).
+__global__ void order_parameters_kernel(kpm_model m, const double* __restrict__ phi, const double* __restrict__ p,
+                                        double* __restrict__ delta_out, double* __restrict__ mag_out) {
+  const int nx = m.nx, ny = m.ny, N = nx * ny;
+  const Layout L{N};
+  const bool gutz = m.gutzwiller != 0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const SiteF si = site_factors(L.n(p, 0, i), L.n(p, 1, i), gutz);
+  Cplx dsum = cx(0.0, 0.0);
+  double rsum = 0.0;
+  for (int e = 0; e < 4; ++e) {
+    const int j = shift(i, kNnX[e], kNnY[e], nx, ny);
+    const SiteF sj = site_factors(L.n(p, 0, j), L.n(p, 1, j), gutz);
+    // phase of the bond i -> j: forward +x/+y stored at i, -x/-y minus the forward phase at j
+    const double ph = e < 2 ? phi[e * N + i] : -phi[(e - 2) * N + j];
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const Cplx term = cadd(cscale(L.F(p, e, i), si.gt[0] * sj.gt[0]), cscale(L.F(p, (e + 2) & 3, j), si.gt[1] * sj.gt[1]));
+    dsum = cadd(dsum, cscale(cmul(term, cx(cs, sn)), e == 1 || e == 3 ? -1.0 : 1.0));
+    // exchange ratio R of the bond (stored at its forward end)
+    const int d = e & 1;
+    const int a = e < 2 ? i : j, b = e < 2 ? j : i;
+    const SiteF& sa = e < 2 ? si : sj;
+    const SiteF& sb = e < 2 ? sj : si;
+    const BondX bx = bond_exchange(sa, sb, L.chi(p, 0, d, a), L.chi(p, 1, d, a), L.F(p, d, a), L.F(p, d + 2, b),
+                                   m.J, gutz);
+    rsum += sqrt(bx.R);
+  }
+  delta_out[2 * i] = dsum.re / 8.0;
+  delta_out[2 * i + 1] = dsum.im / 8.0;
+  const int x = i % nx, y = i / nx;
+  mag_out[i] = ((x + y) & 1 ? -1.0 : 1.0) * si.gxy / 4.0 * rsum * si.m;
+}
+
+cudaError_t launch_order_parameters(const kpm_model& m, const double* phi, const double* params, double* delta_out,
+                                    double* mag_out, cudaStream_t s) {
+  const int N = m.nx * m.ny;
+  order_parameters_kernel<<<(N + 127) / 128, 128, 0, s>>>(m, phi, params, delta_out, mag_out);
+  return cudaGetLastError();
+}
+
 __global__ void gt_weights_kernel(kpm_model m, const double* __restrict__ params, double* __restrict__ w) {
   const int N = m.nx * m.ny;
   const Layout L{N};

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "rmft_iterate": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts),
                                     ctypes.POINTER(kpm_rmft_opts), _P, _P, _P, ctypes.c_int,
                                     ctypes.POINTER(kpm_rmft_stats), _P]),
+    "kpm_order_parameters": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), _P, _P, _P, _P, _P]),
     "kpm_ldos": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P, ctypes.c_int,
                                 _P, ctypes.c_double, ctypes.c_double, _P, _P]),
     "kpm_observables_noalloc": (ctypes.c_int, [ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P,
@@ -271,3 +272,10 @@ def kpm_ldos(ctx: Context, model, opts, fields, ab, params, omega, ldos, gamma_a
     return ctx.check(ctx.lib.kpm_ldos(ctx.handle, ctypes.byref(model), ctypes.byref(opts), _ptr(fields), _ptr(ab),
                                       _ptr(params), int(len(omega)), _ptr(omega), float(gamma_alpha), float(gamma0),
                                       _ptr(ldos), _stream(stream)), "kpm_ldos")
+
+
+def kpm_order_parameters(ctx: Context, model, phi, params, delta_out, mag_out, stream=None):
+    """Physical pairing Delta_i (2N doubles: re, im) and staggered magnetisation M_i (N)."""
+    return ctx.check(ctx.lib.kpm_order_parameters(ctx.handle, ctypes.byref(model), _ptr(phi), _ptr(params),
+                                                  _ptr(delta_out), _ptr(mag_out), _stream(stream)),
+                     "kpm_order_parameters")
