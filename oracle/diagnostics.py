@@ -11,7 +11,8 @@ the exponent depends on the hopping convention.
 
 Eq. gm: the staggered magnetisation
     M_i = (-1)^{x+y} g^{s,xy}_i / 4 sum_tau sqrt(g^{s,z}_{i,i+tau} / g^{s,xy}_{i,i+tau}) m_i,
-with g^{s,z}/g^{s,xy} = R of the bond (reading W3).
+with g^{s,z}/g^{s,xy} = R of the bond (reading W3); where R < 0 (possible for
+magnetic states away from a solution) the square root, and M_i, is NaN.
 """
 from __future__ import annotations
 
