@@ -401,7 +401,12 @@ def run_ours(args):
         a1.record(stream)
         torch.cuda.synchronize()
         t64 = a0.elapsed_time(a1) / 1e3 * (M - 1) / (Ms - 1)
+        # FP64 step: 13 complex multiply-adds and one complex subtraction per
+        # row-column (106 flops) against the nominal 1.25 TFLOP/s FP64 rate
+        fp64_tflops = 106.0 * D * D * (M - 1) / t64 / 1e12
         fp64 = {"s_per_pass": t64, "vector_moments_per_s": D * M / t64,
+                "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": 1.25, "unit": "TFLOP/s",
+                             "frac": fp64_tflops / 1.25, "peak_kind": "nominal FP64 rate"},
                 "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
                 "fp32_speedup": t64 / (t / args.steps)}
 
