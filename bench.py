@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-ldos", action="store_true", help="skip the LDOS section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
+    ap.add_argument("--lbfgs-study", action="store_true",
+                    help="64x64 fixed-point loop against the L-BFGS driver (field residual vs passes) and exit")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
     ap.add_argument("--profile-small", action="store_true",
@@ -692,6 +694,55 @@ def adjoint_section(kpm, inputs, torch):
             "backward_over_forward": tb / tf, "store_all": store_all}
 
 
+def lbfgs_study(warm=50, steps_fp=250, iters_lbfgs=40):
+    """The 64x64 adjoint cell (M = 1024, FP32): from the state of `warm`
+    fixed-point iterations on the vortex seed, the fixed-point loop and the
+    L-BFGS driver over the effective fields (driven by kpm_backward, chemical
+    potential held at the warm state's) as field-space residual against KPM
+    passes (a backward pass counted as one pass) and wall time."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm, lbfgs
+    build.build()
+    w = inputs.CFG4
+    N, M = w.n_sites, w.M
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    p0 = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    opts = kpm.make_opts(M, kpm.KPM_FP32)
+    ropts = kpm.make_rmft_opts(w.n_target, tol=0.0)
+    t0 = time.perf_counter()
+    p = p0.clone()
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _, st = kpm.rmft_iterate(ctx, model, opts, ropts, phi, p, mu, warm)
+    p_warm, mu_warm = p.clone(), st.mu
+    th = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, p, st.mu, th)
+    r_warm = lbfgs.FieldProblem(ctx, model, opts, phi, st.mu, th).residual(th)
+    fp_trace = [(0, r_warm, st.residual)]
+    done = 0
+    while done < steps_fp:
+        _, st = kpm.rmft_iterate(ctx, model, opts, ropts, phi, p, mu, 25)
+        done += 25
+        kpm.kpm_build_H(ctx, model, phi, p, st.mu, th)
+        prob = lbfgs.FieldProblem(ctx, model, opts, phi, st.mu, th)
+        fp_trace.append((done, prob.residual(th), st.residual))
+    t_fp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lb_trace = []
+    _, _, info = lbfgs.rmft_lbfgs(ctx, model, opts, phi, p_warm, mu_warm, max_iter=iters_lbfgs, tol=0.0,
+                                  trace=lb_trace)
+    t_lb = time.perf_counter() - t0
+    kpm.kpm_destroy(ctx)
+    out = {"cell": "64x64", "M": M, "precision": "fp32", "warm_start_iterations": warm,
+           "warm_field_residual": r_warm,
+           "fixed_point": {"trace_iterations_field_residual_param_residual": fp_trace, "wall_s": t_fp},
+           "lbfgs": {"trace_passes_field_residual": lb_trace, "wall_s": t_lb, "info": info}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def profile_adjoint(full=False):
     """Adjoint case for ncu: the 64x64 cell, FP32.  Small (default): M = 64,
     checkpoints every 8 moments, slabs of 2048 columns (134 MB per slab
@@ -755,6 +806,8 @@ def main():
     args = parse()
     if args.profile_small:
         return profile_small(args.double_step)
+    if args.lbfgs_study:
+        return lbfgs_study()
     if args.profile_adjoint:
         return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":

@@ -75,6 +75,14 @@ class FieldProblem:
         self.last_residual = float(r.abs().max())
         return 0.5 * torch.dot(r, r), grad
 
+    def residual(self, theta):
+        """max |g(fields(O(theta))) - g(theta)| without the gradient (one pass)."""
+        N = self.N
+        kpm.kpm_observables(self.ctx, self.model, self.opts, theta, self.ab, self.obs, self.omega)
+        kpm.kpm_build_H(self.ctx, self.model, self.phi, self.obs, self.mu, self.fW, self.w)
+        self.passes += 1
+        return float((_dual(self.fW, N) - _dual(theta, N)).abs().max())
+
     def physical(self):
         """Every site density of the last evaluation lies in (0, 1)."""
         N = self.N
@@ -91,7 +99,7 @@ def _inside(ctx, model, theta, ab_fixed, scratch):
     return (b1 - a1 >= b0 - a0) and (b1 + a1 <= b0 + a0)
 
 
-def rmft_lbfgs(ctx, model, opts, phi, params0, mu, max_iter=200, tol=1e-9, history=20, widen=0.05):
+def rmft_lbfgs(ctx, model, opts, phi, params0, mu, max_iter=200, tol=1e-9, history=20, widen=0.05, trace=None):
     """Minimise Phi over the fields starting from the fields of params0.
 
     Limited-memory BFGS (two-loop recursion) with an Armijo backtracking line
@@ -99,7 +107,8 @@ def rmft_lbfgs(ctx, model, opts, phi, params0, mu, max_iter=200, tol=1e-9, histo
     non-finite values, or with a site density outside (0, 1).  Stops when the
     largest field-space residual component is below tol.  Returns (theta, obs, info) with info =
     {iterations, passes, phi, grad_max, field_residual}, field_residual =
-    max |fields(O(theta)) - theta|.
+    max |fields(O(theta)) - theta|.  trace: optional list that receives
+    (KPM passes so far, field residual) after every accepted step.
     """
     N = model.nx * model.ny
     x = torch.empty(26 * N, dtype=torch.float64, device=params0.device)
@@ -154,6 +163,8 @@ def rmft_lbfgs(ctx, model, opts, phi, params0, mu, max_iter=200, tol=1e-9, histo
                 S.pop(0)
                 Y.pop(0)
         x, f, g = xn, fn, gn
+        if trace is not None:
+            trace.append((prob.passes, prob.last_residual))
     prob.value_and_grad(x)
     info = {"iterations": it, "passes": prob.passes, "objective": f, "grad_max": float(g.abs().max()),
             "field_residual": prob.last_residual}
