@@ -561,6 +561,7 @@ def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
     rows = []
     for p in (5, 10, 20, 25):
         o = kpm.make_opts(M, kpm.KPM_FP32, probe_p=p, probe_seed=1)
+        o, _ = kpm.kpm_autotune(ctx, model, o, fields, ab)  # slab of R columns: its own launch shape
         kpm.kpm_observables(ctx, model, o, fields, ab, est)
         torch.cuda.synchronize()
         ev[0].record()
@@ -578,7 +579,8 @@ def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
         kpm.rmft_iterate(ctx, model, o, ropts, phi, pp, mu, args.steps)
         ev[1].record()
         torch.cuda.synchronize()
-        rows.append({"p": p, "R": 2 * p * p, "s_per_pass": t_pass,
+        rows.append({"p": p, "R": 2 * p * p, "s_per_pass": t_pass, "cols_per_block": o.cols_per_block,
+                     "two_steps_per_launch": bool(o.flags & kpm.KPM_FLAG_DOUBLE_STEP),
                      "s_per_rmft_iteration": ev[0].elapsed_time(ev[1]) / 1e3 / args.steps,
                      "max_err_n": float(d[:2 * N].max()), "max_err_chi": float(d[2 * N:18 * N].max()),
                      "max_err_F": float(d[18 * N:].max())})
