@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-ldos", action="store_true", help="skip the LDOS section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
+    ap.add_argument("--profile-probing", action="store_true",
+                    help="one probing pass (100x100, p = 10, M = 64) for ncu launch lists, and exit")
     ap.add_argument("--lbfgs-study", action="store_true",
                     help="64x64 fixed-point loop against the L-BFGS driver (field residual vs passes) and exit")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
@@ -777,6 +779,32 @@ def profile_adjoint(full=False):
     return 0
 
 
+def profile_probing():
+    """Probing pass for ncu launch lists: the benchmark lattice, p = 10
+    (R = 200 vectors, an L2-resident slab), M = 64."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    w = inputs.CFG2
+    N = w.n_sites
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    kpm.kpm_observables(ctx, model, kpm.make_opts(64, kpm.KPM_FP32, probe_p=10, probe_seed=1), fields, ab, obs)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(obs).all())
+    kpm.kpm_destroy(ctx)
+    print("profile-probing done")
+    return 0
+
+
 def profile_small(double_step=False):
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
     (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
@@ -808,6 +836,8 @@ def main():
     args = parse()
     if args.profile_small:
         return profile_small(args.double_step)
+    if args.profile_probing:
+        return profile_probing()
     if args.lbfgs_study:
         return lbfgs_study()
     if args.profile_adjoint:
