@@ -76,3 +76,33 @@ def f_probing(h, a, b, M, nx, ny, p, seed, T=0.0):
 def observables_probing(model, h, a, b, M, p, seed, T=0.0):
     F, omega = f_probing(h, a, b, M, model.nx, model.ny, p, seed, T)
     return observables(model, F), omega
+
+
+def columns_probing_naive(hcsr, a, b, M, nx, ny, p, seed, cols_of):
+    """Probing estimates of the columns of F_M(h~) whose row has one of the
+    given colours, by the Chebyshev recursion on those probing vectors (for
+    large lattices): returns (J, F) with F[:, k] = conj(xi_J) F_M(h~) r_colour(J)
+    for the rows J of those colours."""
+    import scipy.sparse as sps
+    D = hcsr.shape[0]
+    cl = colours(nx, ny, p)
+    xi = phases(D, seed)
+    cols_of = np.asarray(cols_of)
+    R = np.zeros((D, len(cols_of)), dtype=np.complex128)
+    for k, col in enumerate(cols_of):
+        rows = np.nonzero(cl == col)[0]
+        R[rows, k] = xi[rows]
+    ht = (hcsr - b * sps.identity(D, dtype=np.complex128, format="csr")) / a
+    am, _ = coefficients(M, a, b)
+    V0 = R
+    acc = am[0] * V0
+    if M > 1:
+        V1 = ht @ V0
+        acc = acc + am[1] * V1
+        for m in range(2, M):
+            V0, V1 = V1, 2.0 * (ht @ V1) - V0
+            acc = acc + am[m] * V1
+    J = np.nonzero(np.isin(cl, cols_of))[0]
+    idx = {int(col): k for k, col in enumerate(cols_of)}
+    F = np.stack([np.conj(xi[j]) * acc[:, idx[int(cl[j])]] for j in J], axis=1)
+    return J, F

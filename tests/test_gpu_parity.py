@@ -251,7 +251,7 @@ def test_full_size_vortex_sampled_columns(K):
     sites = np.concatenate([[0, nx - 1, nx * ny - 1, 25 + 50 * nx], rng.choice(nx * ny, 4, replace=False)])
     cols = np.sort(np.concatenate([2 * sites, 2 * sites + 1]))
     Fc, _ = okpm.f_naive(bdg.csr(orm, f), a, b, w.M, cols=cols)
-    full = np.zeros((2 * nx * ny, 2 * nx * ny), dtype=np.complex128)
+    full = np.zeros((2 * nx * ny, 2 * nx * ny), dtype=np.complex128, order="F")
     full[:, cols] = Fc
     ref = okpm.observables(orm, full)
     gn, gc, gF = rmft.split(obs, nx * ny)

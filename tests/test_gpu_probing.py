@@ -107,3 +107,37 @@ def test_invalid_colourings_are_refused(K):
                 dict(probe_p=2, flags=kpm.KPM_FLAG_PH_HALF)):
         with pytest.raises(kpm.KPMError):
             _gpu(K, model, fields, ab, kpm.make_opts(32, kpm.KPM_FP64, **bad))
+
+
+def test_full_size_probing_sampled_colours(K):
+    """100 x 100 two-vortex cell with the PDW seed, M = 2048, FP32, p = 10
+    (R = 200) as benchmarked: every site of two colour classes against the
+    oracle's recursion on those probing vectors."""
+    kpm, ctx = K
+    w = inputs.CFG2
+    nx, ny, N = w.nx, w.ny, w.n_sites
+    p = inputs.vortex_seed(w)
+    model = kpm.make_model(nx, ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, torch.tensor(p, device="cuda"), 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    got, _ = _gpu(K, model, fields, ab, kpm.make_opts(w.M, kpm.KPM_FP32, probe_p=10, probe_seed=1))
+    orm = rmft.Model(nx, ny)
+    f = rmft.fields(orm, p, 0.0)
+    a, b = bdg.gershgorin(orm, f)
+    assert ab.cpu().numpy() == pytest.approx([a, b], rel=1e-13)
+    colours = [0, 1, 146, 147]  # both Nambu rows of the sites (x, y) = (0, 0) and (3, 7) mod 10
+    J, F = probing.columns_probing_naive(bdg.csr(orm, f), a, b, w.M, nx, ny, 10, 1, colours)
+    full = np.zeros((2 * N, 2 * N), dtype=np.complex128, order="F")
+    full[:, J] = F
+    ref = okpm.observables(orm, full)
+    sites = np.unique(J // 2)
+    assert len(sites) == 200
+    gn, gc, gF = rmft.split(got, N)
+    rn, rc, rF = rmft.split(ref, N)
+    assert np.max(np.abs(gn[:, sites] - rn[:, sites])) < 2e-5
+    assert np.max(np.abs(gc[:, :, sites] - rc[:, :, sites])) < 2e-5
+    assert np.max(np.abs(gF[:, sites] - rF[:, sites])) < 2e-5

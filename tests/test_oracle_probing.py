@@ -79,3 +79,18 @@ def test_error_falls_with_colour_spacing():
             for p in (2, 3, 4, 6, 12)]
     assert errs[-1] < 1e-12
     assert errs[0] > errs[2] > errs[3] > errs[-1]
+
+
+def test_recursion_route_equals_spectral_route():
+    # the naive recursion on selected probing vectors reproduces the dense estimate
+    nx = ny = 6
+    model, h, a, b = _cell(nx, ny)
+    M, p, seed = 48, 3, 7
+    dense, _ = probing.f_probing(h, a, b, M, nx, ny, p, seed)
+    fld_model = rmft.Model(nx, ny)
+    w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), 64)
+    from oracle import bdg as _bdg
+    fld = rmft.fields(fld_model, inputs.vortex_seed(w), 0.3)
+    J, F = probing.columns_probing_naive(_bdg.csr(fld_model, fld), a, b, M, nx, ny, p, seed, [0, 1, 7])
+    assert len(J) == 3 * (nx // p) * (ny // p)
+    assert np.max(np.abs(F - dense[:, J])) < 1e-12
