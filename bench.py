@@ -377,7 +377,9 @@ def run_ours(args):
     alg_bytes = rec_bytes / max(rec_launches, 1)
     vecs_per_launch = alg_bytes / (D * ldv * 8)
     dbl = vecs_per_launch > 3.5
-    kname = "cheb_step2_f32_kernel" if dbl else "cheb_step_f32_kernel<16,1>"
+    # single step: chunks of 8 or 16 columns run the TMA-staged kernel
+    kname = "cheb_step2_f32_kernel" if dbl else (
+        "cheb_step_f32_tma_kernel<%d,1>" % cb if cb >= 8 else "cheb_step_f32_kernel<%d,1>" % cb)
     pk, pk_kind = peaks()
     achieved = rec_bytes / (rec_ms / 1e3) / 1e9
     nslab = 4 if dbl else 2

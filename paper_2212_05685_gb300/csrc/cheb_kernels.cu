@@ -18,16 +18,20 @@
 // stores each column pair (2p, 2p+1) as (re_2p, re_2p+1, im_2p, im_2p+1) so
 // that one packed f32x2 FMA advances two columns.  h~ is a 13-point stencil
 // per row (diagonal, eight hops, four pairings), read from a per-site table
-// of 2h~ entries (FP32: each entry duplicated as (re, re, im, im)).
+// of kCoef complex 2h~ entries.
 //
 // Each CTA owns a chunk of CB columns and a band of lattice rows y0..y1-1.  It
 // marches along y keeping lattice rows y-1, y, y+1 of V_m (all Nx sites, both
-// Nambu components, CB columns) in shared memory, with row y+2 and the next
-// coefficient row in flight through cp.async, so every V_m element is read
-// from global memory once per CTA while serving the 13 rows that need it.
+// Nambu components, CB columns) in shared memory, with the next rows and
+// coefficient rows in flight (FP32 chunks of 8 or 16 columns: TMA tensor and
+// bulk copies completing on mbarriers; otherwise cp.async), so every V_m
+// element is read from global memory once per CTA while serving the 13 rows
+// that need it.
 // V_{m-1} is read ahead (FP32: into registers one row early; FP64: through
 // cp.async) and V_{m+1} written in place with coalesced 16-byte accesses.
 // No tensor cores: the stencil is sparse, not a dense contraction.
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "kpm_internal.cuh"
@@ -581,6 +585,251 @@ __global__ void __launch_bounds__(512, 1)
   f32_step_body<CB, MODE>(nx, ny, D, ldv, ylen, table, Vcur, Vprev, Vout, cmap, acc, am, ao, m);
 }
 
+// ---- FP32 step with TMA staging ------------------------------------------
+// Same stencil, ring depths, arithmetic and results as f32_step_body; the
+// V_m window rows and the coefficient rows are moved by the tensor memory
+// accelerator instead of per-thread cp.async: one elected thread issues, per
+// lattice row, a 2-D tensor copy of the row's 2 Nx Nambu rows x CB columns
+// (cp.async.bulk.tensor, one box or a few row boxes) and a 1-D bulk copy of
+// the row's 2h~ entries, each completing on an mbarrier of its ring slot with
+// the byte count expected; every thread waits on the slots it reads.  The
+// block barrier per lattice row stays (it frees the ring slot of row y-2).
+// Waits are bounded in time: a CTA whose copies do not land sets the fault
+// word, waits (bounded) for its copies in flight and writes NaN over its
+// output rows, so a failed launch shows in the observables instead of
+// hanging the device.
+__device__ unsigned int g_step_fault;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// true once the phase of parity `parity` has completed; false after about
+// limit_ns of waiting (or 2^26 polls)
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < (1u << 26); ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  return mbar_try(bar, parity) || mbar_wait_slow(bar, parity, limit_ns);
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: orders of magnitude above a lattice row's copies
+
+template <int CB, int MODE>
+__device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx, int ny, int64_t D, int64_t ldv,
+                                                  int ylen, int brows, const float2* __restrict__ table,
+                                                  const float4* Vprev, float4* Vout, ColMap cmap,
+                                                  double2* __restrict__ acc, const double* __restrict__ am,
+                                                  const double* __restrict__ ao, int m) {
+  constexpr int NV = CB / 2;
+  constexpr int RS = 2 * NV;
+  const int64_t ldq = ldv / 2;
+
+  extern __shared__ __align__(1024) unsigned char smem_tma[];
+  float4* win = reinterpret_cast<float4*>(smem_tma);                       // [5][nx][2][NV]
+  float2* coef = reinterpret_cast<float2*>(win + 5 * nx * RS);             // [3][nx][kCoef]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(coef + 3 * nx * kCoef);    // V slots 0..4, coef slots 5..7
+  const int rowsz = nx * RS;
+  const int crow = nx * kCoef;
+
+  const int64_t cb0 = (int64_t)blockIdx.y * CB;
+  const int64_t q0 = cb0 / 2;
+  const int y0 = blockIdx.x * ylen;
+  const int y1 = min(ny, y0 + ylen);
+  const int nrow = y1 - y0;
+
+  const int v = threadIdx.x % NV;
+  const int xs = threadIdx.x / NV;
+  const int xstep = blockDim.x / NV;
+  const bool own0 = xs < nx, own1 = xs + xstep < nx;
+
+  int yj_lo = ny, yj_hi = -1;
+  {
+    const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
+    if (cmap.probe_p) {
+      yj_lo = 0;
+      yj_hi = ny - 1;
+    } else if (chi >= clo) {
+      yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
+      yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
+    }
+  }
+
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t vbytes = (uint32_t)(2 * nx * CB * 8);  // one window row: 2 Nx Nambu rows x CB complex FP32
+  const uint32_t cbytes = (uint32_t)(nx * kCoef * 8);   // one coefficient row
+  const int nbox = 2 * nx / brows;
+  // window row w holds lattice row y0 - 1 + w (w = 0 .. nrow + 1) in slot w % 5,
+  // coefficient row c holds row y0 + c (c = 0 .. nrow - 1) in slot c % 3
+  auto issue_v = [&](int w) {
+    const int ly = wrapi(y0 - 1 + w, ny);
+    const uint32_t bar = bar0 + 8 * (w % 5);
+    const uint32_t dst = smem_u32(win + (w % 5) * rowsz);
+    mbar_expect_tx(bar, vbytes);
+    for (int b = 0; b < nbox; ++b)
+      tma_load_2d(dst + (uint32_t)(b * brows * CB * 8), tm, (int)(2 * cb0), 2 * nx * ly + b * brows, bar);
+  };
+  auto issue_c = [&](int c) {
+    const uint32_t bar = bar0 + 8 * (5 + c % 3);
+    mbar_expect_tx(bar, cbytes);
+    bulk_load(smem_u32(coef + (c % 3) * crow), table + (int64_t)(y0 + c) * crow, cbytes, bar);
+  };
+  auto vbar = [&](int w) { return bar0 + 8 * (w % 5); };
+  auto vpar = [&](int w) { return (uint32_t)((w / 5) & 1); };
+
+  auto poison = [&]() {  // NaN over the CTA's output rows
+    const float nan = __int_as_float(0x7fc00000);
+    const float4 nan4 = make_float4(nan, nan, nan, nan);
+    for (int t = threadIdx.x; t < nrow * 2 * nx * NV; t += blockDim.x) {
+      const int r = t / NV, c = t - r * NV;
+      Vout[((int64_t)2 * nx * y0 + r) * ldq + q0 + c] = nan4;
+    }
+  };
+  // after a fault anywhere, later CTAs and launches only mark their outputs
+  if (*reinterpret_cast<volatile unsigned int*>(&g_step_fault) != 0u) {
+    poison();
+    return;
+  }
+  const bool aligned = (smem_u32(win) & 127u) == 0;
+  if (aligned && threadIdx.x == 0) {
+    for (int k = 0; k < 8; ++k) mbar_init(bar0 + 8 * k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  if (!__syncthreads_and(aligned)) {
+    if (threadIdx.x == 0) atomicOr(&g_step_fault, 2u);
+    poison();
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int w = 0; w <= min(3, nrow + 1); ++w) issue_v(w);
+    for (int c = 0; c <= min(1, nrow - 1); ++c) issue_c(c);
+  }
+
+  ulonglong2 pc[2][2], pn[2][2];
+  const ulonglong2 zero2 = make_ulonglong2(0ull, 0ull);
+  auto load_prev = [&](int y, ulonglong2 (&dst)[2][2]) {
+    const float4* g = Vprev + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
+    const int64_t gstep = 2 * (int64_t)xstep * ldq;
+    dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
+    dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
+    dst[1][0] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep) : zero2;
+    dst[1][1] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep + ldq) : zero2;
+  };
+  if (MODE == 1) load_prev(y0, pc);
+
+  const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
+  int failed_at = -1;
+  for (int q = 0; q < nrow; ++q) {
+    const int y = y0 + q;
+    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, pn);
+    bool ok = true;
+    if (q == 0) ok = mbar_wait(vbar(0), 0, kWaitLimitNs) && mbar_wait(vbar(1), 0, kWaitLimitNs);
+    ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), kWaitLimitNs) &&
+         mbar_wait(bar0 + 8 * (5 + q % 3), (uint32_t)((q / 3) & 1), kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+      failed_at = q;
+      break;
+    }
+    // every thread is past row y-1: window row y+3 into the slot of y-2,
+    // coefficients of y+2 into the slot of y-1
+    if (threadIdx.x == 0) {
+      if (q + 4 <= nrow + 1) issue_v(q + 4);
+      if (q + 2 < nrow) issue_c(q + 2);
+    }
+    const float4* wm = win + (q % 5) * rowsz + v;
+    const float4* w0 = win + ((q + 1) % 5) * rowsz + v;
+    const float4* wp = win + ((q + 2) % 5) * rowsz + v;
+    const float2* cf_row = coef + (q % 3) * crow;
+
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      if (!(it == 0 ? own0 : own1)) continue;
+      const int x = xs + it * xstep;
+      ulonglong2 o0, o1;
+      stencil_site<NV>(wm, w0, wp, cf_row, x, nx, o0, o1);
+      if (MODE == 1) {
+        o0.x = f2sub(o0.x, pc[it][0].x);
+        o0.y = f2sub(o0.y, pc[it][0].y);
+        o1.x = f2sub(o1.x, pc[it][1].x);
+        o1.y = f2sub(o1.y, pc[it][1].y);
+      } else {
+        o0.x = f2mul(o0.x, half2);
+        o0.y = f2mul(o0.y, half2);
+        o1.x = f2mul(o1.x, half2);
+        o1.y = f2mul(o1.y, half2);
+      }
+      float4* g = Vout + (2 * ((int64_t)y * nx + x)) * ldq + q0 + v;
+      *reinterpret_cast<ulonglong2*>(g) = o0;
+      *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
+    }
+
+    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, m, am[m], ao[m], acc);
+    if (MODE == 1) {
+      pc[0][0] = pn[0][0];
+      pc[0][1] = pn[0][1];
+      pc[1][0] = pn[1][0];
+      pc[1][1] = pn[1][1];
+    }
+  }
+  if (failed_at >= 0) {
+    // copies possibly in flight: window rows failed_at .. failed_at + 3 and
+    // coefficient rows failed_at, failed_at + 1 (all earlier ones completed)
+    const int q = failed_at;
+    if (threadIdx.x == 0) {
+      atomicOr(&g_step_fault, 1u);
+      for (int w = q; w <= min(q + 3, nrow + 1); ++w) mbar_wait(vbar(w), vpar(w), kWaitLimitNs / 4);
+      for (int c = q; c <= min(q + 1, nrow - 1); ++c)
+        mbar_wait(bar0 + 8 * (5 + c % 3), (uint32_t)((c / 3) & 1), kWaitLimitNs / 4);
+    }
+    poison();
+  }
+}
+
+template <int CB, int MODE>
+__global__ void __launch_bounds__(512, 1)
+    cheb_step_f32_tma_kernel(const __grid_constant__ CUtensorMap tm, int nx, int ny, int64_t D, int64_t ldv,
+                             int ylen, int brows, const float2* __restrict__ table, const float4* Vprev, float4* Vout,
+                             ColMap cmap, double2* __restrict__ acc, const double* __restrict__ am,
+                             const double* __restrict__ ao, int m) {
+  f32_step_body_tma<CB, MODE>(&tm, nx, ny, D, ldv, ylen, brows, table, Vprev, Vout, cmap, acc, am, ao, m);
+}
+
 // FP32 double step: two recursion steps per launch (Eq. alpha applied twice),
 // from V_{m-1} (Vprev) and V_m (Vcur) to V_{m+1} (Vout1) and V_{m+2} (Vout2),
 // all four slabs distinct.  Per pair of steps the slabs are streamed once
@@ -877,6 +1126,7 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kTmaBarBytes = 8 * sizeof(uint64_t);  // mbarriers of the TMA step (5 window + 3 coefficient slots)
 constexpr int kSMs = 152;
 
 template <int CB>
@@ -915,8 +1165,47 @@ cudaError_t set_smem_f32(int nx) {
   cudaError_t e = cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kSmemLimit);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kSmemLimit);
+  e = cudaFuncSetAttribute(cheb_step_f32_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSmemLimit);
+  if (e != cudaSuccess || CB < 8) return e;
+  e = cudaFuncSetAttribute(cheb_step_f32_tma_kernel<CB >= 8 ? CB : 8, 0>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_f32_tma_kernel<CB >= 8 ? CB : 8, 1>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+}
+
+// cuTensorMapEncodeTiled, resolved once through the runtime's driver entry point
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of an FP32 pair-split slab V[D][ldv] viewed as D rows of 2 ldv
+// floats; box: 2 cb floats (the chunk's cb complex columns) x brows Nambu rows
+cudaError_t encode_slab_map(CUtensorMap* tm, const void* V, int64_t D, int64_t ldv, int cb, int brows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ldv), (cuuint64_t)D};
+  const cuuint64_t strides[1] = {(cuuint64_t)(8 * ldv)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * cb), (cuuint32_t)brows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(V), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 template <int CB>
 cudaError_t set_smem_f32_batched(int nx) {
@@ -949,6 +1238,22 @@ template <int CB>
 cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, const void* Vprev, void* Vout,
                        int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
+  if (CB >= 8 && p.tma_rows > 0) {
+    constexpr int CT = CB >= 8 ? CB : 8;
+    CUtensorMap tm;
+    const cudaError_t e = encode_slab_map(&tm, Vcur, p.D, p.ldv, CB, p.tma_rows);
+    if (e != cudaSuccess) return e;
+    const size_t sm = p.smem + kTmaBarBytes;
+    if (mode == 0)
+      cheb_step_f32_tma_kernel<CT, 0><<<grid, p.nthreads, sm, s>>>(
+          tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, (const float2*)table, (const float4*)Vprev, (float4*)Vout,
+          colmap(p, s0), acc, am, ao, m);
+    else
+      cheb_step_f32_tma_kernel<CT, 1><<<grid, p.nthreads, sm, s>>>(
+          tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, (const float2*)table, (const float4*)Vprev, (float4*)Vout,
+          colmap(p, s0), acc, am, ao, m);
+    return cudaGetLastError();
+  }
   if (mode == 0)
     cheb_step_f32_kernel<CB, 0><<<grid, p.nthreads, p.smem, s>>>(p.nx, p.ny, p.D, p.ldv, p.ylen, (const float2*)table,
                                                                  (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
@@ -1005,6 +1310,18 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
     if (sm <= kSmemLimit) {
       p.cb = c[k];
       p.smem = sm;
+      break;
+    }
+  }
+  p.tma_rows = 0;
+  if (precision == KPM_FP32 && p.cb >= 8 && p.smem + kTmaBarBytes <= kSmemLimit) {
+    // TMA staging: the 2 Nx Nambu rows of a window row in nb equal boxes of
+    // at most 256 rows, each landing on a 128-byte boundary of shared memory
+    const int rows = 2 * nx;
+    for (int nb = (rows + 255) / 256; nb <= rows; ++nb) {
+      if (rows % nb) continue;
+      const int br = rows / nb;
+      if ((br * p.cb * 8) % 128 == 0) p.tma_rows = br;
       break;
     }
   }
