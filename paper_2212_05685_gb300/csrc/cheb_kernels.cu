@@ -753,18 +753,17 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   if (MODE == 1) load_prev(y0, pc);
 
   const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
-  int failed_at = -1;
-  for (int q = 0; q < nrow; ++q) {
+  // one lattice row; V_{m-1} of row y in `cur`, row y+1 loaded into `nxt`
+  // (the caller alternates the two register sets, so the loads issued here
+  // are first used a full row later); false when a copy did not land
+  auto row = [&](int q, ulonglong2 (&cur)[2][2], ulonglong2 (&nxt)[2][2]) -> bool {
     const int y = y0 + q;
-    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, pn);
+    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, nxt);
     bool ok = true;
     if (q == 0) ok = mbar_wait(vbar(0), 0, kWaitLimitNs) && mbar_wait(vbar(1), 0, kWaitLimitNs);
     ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), kWaitLimitNs) &&
          mbar_wait(bar0 + 8 * (5 + q % 3), (uint32_t)((q / 3) & 1), kWaitLimitNs);
-    if (__syncthreads_or(!ok)) {
-      failed_at = q;
-      break;
-    }
+    if (__syncthreads_or(!ok)) return false;
     // every thread is past row y-1: window row y+3 into the slot of y-2,
     // coefficients of y+2 into the slot of y-1
     if (threadIdx.x == 0) {
@@ -783,10 +782,10 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
       ulonglong2 o0, o1;
       stencil_site<NV>(wm, w0, wp, cf_row, x, nx, o0, o1);
       if (MODE == 1) {
-        o0.x = f2sub(o0.x, pc[it][0].x);
-        o0.y = f2sub(o0.y, pc[it][0].y);
-        o1.x = f2sub(o1.x, pc[it][1].x);
-        o1.y = f2sub(o1.y, pc[it][1].y);
+        o0.x = f2sub(o0.x, cur[it][0].x);
+        o0.y = f2sub(o0.y, cur[it][0].y);
+        o1.x = f2sub(o1.x, cur[it][1].x);
+        o1.y = f2sub(o1.y, cur[it][1].y);
       } else {
         o0.x = f2mul(o0.x, half2);
         o0.y = f2mul(o0.y, half2);
@@ -800,11 +799,17 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
       moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, m, am[m], ao[m], acc);
-    if (MODE == 1) {
-      pc[0][0] = pn[0][0];
-      pc[0][1] = pn[0][1];
-      pc[1][0] = pn[1][0];
-      pc[1][1] = pn[1][1];
+    return true;
+  };
+  int failed_at = -1;
+  for (int q = 0; q < nrow; q += 2) {
+    if (!row(q, pc, pn)) {
+      failed_at = q;
+      break;
+    }
+    if (q + 1 < nrow && !row(q + 1, pn, pc)) {
+      failed_at = q + 1;
+      break;
     }
   }
   if (failed_at >= 0) {
