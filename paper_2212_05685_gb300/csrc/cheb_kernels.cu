@@ -649,6 +649,20 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: orders of magnitude above a lattice row's copies
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Rows without a block barrier: the warps run up to two lattice rows apart.
+// Slot reuse is ordered by a third ring of mbarriers, done[r % 3], on which
+// every warp arrives once it has finished row r (count = warps per CTA); the
+// issuing thread waits for done(r - 1) before it refills the slots that row
+// r - 1 was the last to read.  A warp at row r needs window row r + 2, issued
+// only after done(r - 3), so no warp runs more than two rows ahead of the
+// slowest and no mbarrier phase is reused before it has been waited on.
+// Sites of a row: thread (xs, v) takes site xs, and the nx - xstep sites
+// beyond the first round go to xstep-groups in an order rotated from row to
+// row, so that every warp does the same work averaged over a few rows.
 template <int CB, int MODE>
 __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx, int ny, int64_t D, int64_t ldv,
                                                   int ylen, int brows, const float2* __restrict__ table,
@@ -662,7 +676,8 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   extern __shared__ __align__(1024) unsigned char smem_tma[];
   float4* win = reinterpret_cast<float4*>(smem_tma);                       // [5][nx][2][NV]
   float2* coef = reinterpret_cast<float2*>(win + 5 * nx * RS);             // [3][nx][kCoef]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(coef + 3 * nx * kCoef);    // V slots 0..4, coef slots 5..7
+  uint64_t* bars = reinterpret_cast<uint64_t*>(coef + 3 * nx * kCoef);    // full V 0..4, full coef 5..7, done 8..10
+  volatile int* fail_flag = reinterpret_cast<volatile int*>(bars + 11);
   const int rowsz = nx * RS;
   const int crow = nx * kCoef;
 
@@ -675,7 +690,23 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   const int v = threadIdx.x % NV;
   const int xs = threadIdx.x / NV;
   const int xstep = blockDim.x / NV;
-  const bool own0 = xs < nx, own1 = xs + xstep < nx;
+  const int extra = nx - xstep;  // sites beyond the first round (nx <= 2 xstep, planner)
+  const bool own0 = xs < nx;
+  const int lane = threadIdx.x & 31;
+  // second site of the thread in a row whose extra sites start at xs-group
+  // `rot` (advanced by `rstep` from row to row), or -1
+  const int rstep = extra > 0 ? extra : 0;
+  auto site1 = [&](int rot) {
+    if (extra <= 0) return -1;
+    int d = xs - rot;
+    d = d < 0 ? d + xstep : d;
+    return d < extra ? xstep + d : -1;
+  };
+  auto next_rot = [&](int rot) {
+    rot += rstep;
+    return rot >= xstep ? rot - xstep : rot;
+  };
+  int rot = 0;  // rotation of the CTA's current row
 
   int yj_lo = ny, yj_hi = -1;
   {
@@ -695,6 +726,7 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   const int nbox = 2 * nx / brows;
   // window row w holds lattice row y0 - 1 + w (w = 0 .. nrow + 1) in slot w % 5,
   // coefficient row c holds row y0 + c (c = 0 .. nrow - 1) in slot c % 3
+  int w_hi = -1, c_hi = -1;  // last window / coefficient row issued (issuing thread)
   auto issue_v = [&](int w) {
     const int ly = wrapi(y0 - 1 + w, ny);
     const uint32_t bar = bar0 + 8 * (w % 5);
@@ -702,14 +734,20 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     mbar_expect_tx(bar, vbytes);
     for (int b = 0; b < nbox; ++b)
       tma_load_2d(dst + (uint32_t)(b * brows * CB * 8), tm, (int)(2 * cb0), 2 * nx * ly + b * brows, bar);
+    w_hi = w;
   };
   auto issue_c = [&](int c) {
     const uint32_t bar = bar0 + 8 * (5 + c % 3);
     mbar_expect_tx(bar, cbytes);
     bulk_load(smem_u32(coef + (c % 3) * crow), table + (int64_t)(y0 + c) * crow, cbytes, bar);
+    c_hi = c;
   };
   auto vbar = [&](int w) { return bar0 + 8 * (w % 5); };
   auto vpar = [&](int w) { return (uint32_t)((w / 5) & 1); };
+  auto cbar = [&](int c) { return bar0 + 8 * (5 + c % 3); };
+  auto cpar = [&](int c) { return (uint32_t)((c / 3) & 1); };
+  auto dbar = [&](int r) { return bar0 + 8 * (8 + r % 3); };
+  auto dpar = [&](int r) { return (uint32_t)((r / 3) & 1); };
 
   auto poison = [&]() {  // NaN over the CTA's output rows
     const float nan = __int_as_float(0x7fc00000);
@@ -724,9 +762,11 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     poison();
     return;
   }
-  const bool aligned = (smem_u32(win) & 127u) == 0;
+  const bool aligned = (smem_u32(win) & 127u) == 0 && (blockDim.x & 31) == 0;
   if (aligned && threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) mbar_init(bar0 + 8 * k, 1);
+    for (int k = 8; k < 11; ++k) mbar_init(bar0 + 8 * k, blockDim.x >> 5);
+    *fail_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
@@ -742,43 +782,52 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
 
   ulonglong2 pc[2][2], pn[2][2];
   const ulonglong2 zero2 = make_ulonglong2(0ull, 0ull);
-  auto load_prev = [&](int y, ulonglong2 (&dst)[2][2]) {
+  auto load_prev = [&](int y, int r, ulonglong2 (&dst)[2][2]) {
     const float4* g = Vprev + (2 * ((int64_t)y * nx + xs)) * ldq + q0 + v;
-    const int64_t gstep = 2 * (int64_t)xstep * ldq;
     dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
     dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
-    dst[1][0] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep) : zero2;
-    dst[1][1] = own1 ? *reinterpret_cast<const ulonglong2*>(g + gstep + ldq) : zero2;
+    const int x1 = site1(r);
+    const float4* g1 = Vprev + (2 * ((int64_t)y * nx + (x1 < 0 ? 0 : x1))) * ldq + q0 + v;
+    dst[1][0] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1) : zero2;
+    dst[1][1] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1 + ldq) : zero2;
   };
-  if (MODE == 1) load_prev(y0, pc);
+  if (MODE == 1) load_prev(y0, rot, pc);
 
   const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
   // one lattice row; V_{m-1} of row y in `cur`, row y+1 loaded into `nxt`
   // (the caller alternates the two register sets, so the loads issued here
-  // are first used a full row later); false when a copy did not land
+  // are first used a full row later); false when the CTA gives up
   auto row = [&](int q, ulonglong2 (&cur)[2][2], ulonglong2 (&nxt)[2][2]) -> bool {
     const int y = y0 + q;
-    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, nxt);
+    if (__any_sync(0xffffffffu, *fail_flag != 0)) return false;
+    const int rot_next = next_rot(rot);
+    if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, rot_next, nxt);
     bool ok = true;
     if (q == 0) ok = mbar_wait(vbar(0), 0, kWaitLimitNs) && mbar_wait(vbar(1), 0, kWaitLimitNs);
-    ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), kWaitLimitNs) &&
-         mbar_wait(bar0 + 8 * (5 + q % 3), (uint32_t)((q / 3) & 1), kWaitLimitNs);
-    if (__syncthreads_or(!ok)) return false;
-    // every thread is past row y-1: window row y+3 into the slot of y-2,
-    // coefficients of y+2 into the slot of y-1
-    if (threadIdx.x == 0) {
-      if (q + 4 <= nrow + 1) issue_v(q + 4);
-      if (q + 2 < nrow) issue_c(q + 2);
+    ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), kWaitLimitNs) && mbar_wait(cbar(q), cpar(q), kWaitLimitNs);
+    if (threadIdx.x == 0 && ok) {
+      // window row y+3 into the slot of y-2 and coefficients of y+2 into the
+      // slot of y-1, once every warp has finished row y-1 (row 0: fresh slots)
+      if (q >= 1) ok = mbar_wait(dbar(q - 1), dpar(q - 1), kWaitLimitNs);
+      if (ok) {
+        if (q + 4 <= nrow + 1) issue_v(q + 4);
+        if (q + 2 < nrow) issue_c(q + 2);
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+      *fail_flag = 1;
+      return false;
     }
     const float4* wm = win + (q % 5) * rowsz + v;
     const float4* w0 = win + ((q + 1) % 5) * rowsz + v;
     const float4* wp = win + ((q + 2) % 5) * rowsz + v;
     const float2* cf_row = coef + (q % 3) * crow;
+    const int x1 = site1(rot);
 
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-      if (!(it == 0 ? own0 : own1)) continue;
-      const int x = xs + it * xstep;
+      if (!(it == 0 ? own0 : x1 >= 0)) continue;
+      const int x = it == 0 ? xs : x1;
       ulonglong2 o0, o1;
       stencil_site<NV>(wm, w0, wp, cf_row, x, nx, o0, o1);
       if (MODE == 1) {
@@ -799,29 +848,25 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
       moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, m, am[m], ao[m], acc);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(dbar(q));
+    rot = rot_next;
     return true;
   };
-  int failed_at = -1;
   for (int q = 0; q < nrow; q += 2) {
-    if (!row(q, pc, pn)) {
-      failed_at = q;
-      break;
-    }
-    if (q + 1 < nrow && !row(q + 1, pn, pc)) {
-      failed_at = q + 1;
-      break;
-    }
+    if (!row(q, pc, pn)) break;
+    if (q + 1 < nrow && !row(q + 1, pn, pc)) break;
   }
-  if (failed_at >= 0) {
-    // copies possibly in flight: window rows failed_at .. failed_at + 3 and
-    // coefficient rows failed_at, failed_at + 1 (all earlier ones completed)
-    const int q = failed_at;
+  __syncthreads();
+  if (*fail_flag) {
+    // every copy the CTA issued may still be in flight: wait (bounded) for
+    // the last fill of every slot before the shared memory is released
     if (threadIdx.x == 0) {
       atomicOr(&g_step_fault, 1u);
-      for (int w = q; w <= min(q + 3, nrow + 1); ++w) mbar_wait(vbar(w), vpar(w), kWaitLimitNs / 4);
-      for (int c = q; c <= min(q + 1, nrow - 1); ++c)
-        mbar_wait(bar0 + 8 * (5 + c % 3), (uint32_t)((c / 3) & 1), kWaitLimitNs / 4);
+      for (int w = max(0, w_hi - 4); w <= w_hi; ++w) mbar_wait(vbar(w), vpar(w), kWaitLimitNs / 4);
+      for (int c = max(0, c_hi - 2); c <= c_hi; ++c) mbar_wait(cbar(c), cpar(c), kWaitLimitNs / 4);
     }
+    __syncthreads();
     poison();
   }
 }
@@ -1131,7 +1176,8 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;
-constexpr size_t kTmaBarBytes = 8 * sizeof(uint64_t);  // mbarriers of the TMA step (5 window + 3 coefficient slots)
+// mbarriers of the TMA step (5 window + 3 coefficient slots + 3 row-done) and its fault flag
+constexpr size_t kTmaBarBytes = 16 * sizeof(uint64_t);
 constexpr int kSMs = 152;
 
 template <int CB>
