@@ -592,9 +592,9 @@ __global__ void __launch_bounds__(512, 1)
 // lattice row, a 2-D tensor copy of the row's 2 Nx Nambu rows x CB columns
 // (cp.async.bulk.tensor, one box or a few row boxes) and a 1-D bulk copy of
 // the row's 2h~ entries, each completing on an mbarrier of its ring slot with
-// the byte count expected; every thread waits on the slots it reads.  The
-// block barrier per lattice row stays (it frees the ring slot of row y-2).
-// Waits are bounded in time: a CTA whose copies do not land sets the fault
+// the byte count expected; every thread waits on the slots it reads.  Slot
+// reuse is ordered by row-done mbarriers instead of a block barrier (see the
+// body).  Waits are bounded in time: a CTA whose copies do not land sets the fault
 // word, waits (bounded) for its copies in flight and writes NaN over its
 // output rows, so a failed launch shows in the observables instead of
 // hanging the device.
