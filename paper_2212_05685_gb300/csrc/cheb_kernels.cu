@@ -880,6 +880,21 @@ __global__ void __launch_bounds__(512, 1)
   f32_step_body_tma<CB, MODE>(&tm, nx, ny, D, ldv, ylen, brows, table, Vprev, Vout, cmap, acc, am, ao, m);
 }
 
+// Batched TMA step: blockIdx.z selects the cell; the two slab tensor maps of
+// cell z live in global memory, maps[2 z] over A and maps[2 z + 1] over B;
+// V_m is A at even m and B at odd m (first step: A -> B), in place otherwise
+template <int CB, int MODE>
+__global__ void __launch_bounds__(512, 1)
+    cheb_step_f32_tma_batched_kernel(const CUtensorMap* __restrict__ maps, int nx, int ny, int64_t D, int64_t ldv,
+                                     int ylen, int brows, BatchPtrs b, int m) {
+  const int z = blockIdx.z;
+  const bool cur_b = MODE == 1 && (m & 1);
+  float4* out = reinterpret_cast<float4*>(cur_b ? b.A[z] : b.B[z]);
+  f32_step_body_tma<CB, MODE>(maps + 2 * z + (cur_b ? 1 : 0), nx, ny, D, ldv, ylen, brows,
+                              reinterpret_cast<const float2*>(b.table[z]), out, out,
+                              ColMap{0, 0, 0, 0u, nullptr, nullptr}, b.acc[z], b.am[z], b.ao[z], m);
+}
+
 // FP32 double step: two recursion steps per launch (Eq. alpha applied twice),
 // from V_{m-1} (Vprev) and V_m (Vcur) to V_{m+1} (Vout1) and V_{m+2} (Vout2),
 // all four slabs distinct.  Per pair of steps the slabs are streamed once
@@ -1490,7 +1505,20 @@ cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table
   return cudaErrorInvalidValue;
 }
 
+template <int CB>
+cudaError_t set_smem_f32_tma_batched() {
+  cudaError_t e = cudaFuncSetAttribute(cheb_step_f32_tma_batched_kernel<CB, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_f32_tma_batched_kernel<CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSmemLimit);
+}
+
 cudaError_t cheb_prepare_batched(const ChebPlan& p) {
+  if (p.tma_rows > 0) {
+    const cudaError_t e = p.cb == 16 ? set_smem_f32_tma_batched<16>() : set_smem_f32_tma_batched<8>();
+    if (e != cudaSuccess) return e;
+  }
   switch (p.cb) {
     case 16: return set_smem_f32_batched<16>(p.nx);
     case 8: return set_smem_f32_batched<8>(p.nx);
@@ -1500,8 +1528,29 @@ cudaError_t cheb_prepare_batched(const ChebPlan& p) {
   return cudaErrorInvalidValue;
 }
 
+size_t batch_maps_bytes(int ncell) { return (size_t)2 * ncell * sizeof(CUtensorMap); }
+
+cudaError_t encode_batch_maps(const ChebPlan& p, int ncell, const BatchPtrs& b, void* host_maps) {
+  CUtensorMap* out = static_cast<CUtensorMap*>(host_maps);
+  for (int z = 0; z < ncell; ++z) {
+    cudaError_t e = encode_slab_map(out + 2 * z, b.A[z], p.D, p.ldv, p.cb, p.tma_rows);
+    if (e == cudaSuccess) e = encode_slab_map(out + 2 * z + 1, b.B[z], p.D, p.ldv, p.cb, p.tma_rows);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, const void* maps) {
+  if (maps != nullptr && p.tma_rows > 0 && (p.cb == 16 || p.cb == 8)) {
+    const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / p.cb), (unsigned)ncell);
+    const size_t sm = p.smem + kTmaBarBytes;
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(maps);
+    auto fn = p.cb == 16 ? (mode == 0 ? cheb_step_f32_tma_batched_kernel<16, 0> : cheb_step_f32_tma_batched_kernel<16, 1>)
+                         : (mode == 0 ? cheb_step_f32_tma_batched_kernel<8, 0> : cheb_step_f32_tma_batched_kernel<8, 1>);
+    fn<<<grid, p.nthreads, sm, s>>>(tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, b, m);
+    return cudaGetLastError();
+  }
   switch (p.cb) {
     case 16: return launch_f32_batched<16>(p, ncell, b, m, mode, s);
     case 8: return launch_f32_batched<8>(p, ncell, b, m, mode, s);

@@ -2,6 +2,7 @@
 // ordering of one KPM pass (coefficients, rescaled stencil table, slab
 // recursions, assembly) and of one self-consistency iteration, captured once
 // into a CUDA graph and replayed.
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
 
@@ -82,6 +83,7 @@ struct kpm_ctx {
   size_t bhost_n = 0;
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
+  std::vector<void*> bmaps;        // per shape class: device copy of its cells' slab tensor maps
 
   // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass, probe_p)
   std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> tuned;
@@ -462,6 +464,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
   for (auto& c : ctx->cells)
     if (c.mem) cudaFree(c.mem);
+  for (void* p : ctx->bmaps) cudaFree(p);
   for (cudaStream_t st : ctx->fork) cudaStreamDestroy(st);
   for (cudaEvent_t e : ctx->fork_ev) cudaEventDestroy(e);
   if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
@@ -988,6 +991,43 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     cudaStream_t c0 = ctx->cap;
+    // per shape class: the cells' pointers and, for the TMA-staged step, the
+    // tensor maps of their slabs, uploaded before the capture (the graph
+    // reads them from device memory on every replay)
+    std::vector<BatchPtrs> bps(members.size());
+    std::vector<const void*> maps_of(members.size(), nullptr);
+    for (size_t k = 0; k < members.size(); ++k) {
+      BatchPtrs& bp = bps[k];
+      memset(&bp, 0, sizeof(bp));
+      for (size_t z = 0; z < members[k].size(); ++z) {
+        kpm_ctx::Cell& C = ctx->cells[members[k][z]];
+        bp.A[z] = C.A;
+        bp.B[z] = C.B;
+        bp.table[z] = C.table;
+        bp.acc[z] = C.acc;
+        bp.am[z] = C.am;
+        bp.ao[z] = C.ao;
+      }
+    }
+    if (prec == KPM_FP32) {
+      while (ctx->bmaps.size() < members.size()) {
+        void* d = nullptr;
+        if (cudaMalloc(&d, batch_maps_bytes(kMaxBatch)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(ctx, KPM_ENOMEM, "cudaMalloc of the batch tensor maps failed");
+        }
+        ctx->bmaps.push_back(d);
+      }
+      KPM_CU(cudaStreamSynchronize(c0));  // no replay of an older graph still reads the maps
+      for (size_t k = 0; k < members.size(); ++k) {
+        if (plans[k].tma_rows == 0) continue;
+        const int nz = (int)members[k].size();
+        std::vector<CUtensorMap> host((size_t)2 * nz);
+        KPM_CU(encode_batch_maps(plans[k], nz, bps[k], host.data()));
+        KPM_CU(cudaMemcpy(ctx->bmaps[k], host.data(), batch_maps_bytes(nz), cudaMemcpyHostToDevice));
+        maps_of[k] = ctx->bmaps[k];
+      }
+    }
     KPM_CU(cudaStreamBeginCapture(c0, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     const char* where = "";
@@ -1020,20 +1060,9 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       KPM_TRY(cudaStreamWaitEvent(sk, ctx->join_ev, 0));
       const ChebPlan& p = plans[k];
       if (prec == KPM_FP32) {
-        BatchPtrs bp;
-        memset(&bp, 0, sizeof(bp));
-        for (size_t z = 0; z < members[k].size(); ++z) {
-          kpm_ctx::Cell& C = ctx->cells[members[k][z]];
-          bp.A[z] = C.A;
-          bp.B[z] = C.B;
-          bp.table[z] = C.table;
-          bp.acc[z] = C.acc;
-          bp.am[z] = C.am;
-          bp.ao[z] = C.ao;
-        }
         const int nz = (int)members[k].size();
-        KPM_TRY(launch_cheb_step_batched(p, nz, bp, 0, 0, sk));
-        for (int mm = 1; mm <= M - 2; ++mm) KPM_TRY(launch_cheb_step_batched(p, nz, bp, mm, 1, sk));
+        KPM_TRY(launch_cheb_step_batched(p, nz, bps[k], 0, 0, sk, maps_of[k]));
+        for (int mm = 1; mm <= M - 2; ++mm) KPM_TRY(launch_cheb_step_batched(p, nz, bps[k], mm, 1, sk, maps_of[k]));
       } else {
         for (size_t z = 0; z < members[k].size(); ++z) {
           kpm_ctx::Cell& C = ctx->cells[members[k][z]];

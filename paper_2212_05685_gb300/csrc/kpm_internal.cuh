@@ -117,10 +117,15 @@ cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table
 cudaError_t launch_cheb_step2(const ChebPlan& p, const void* table, const void* Vprev, const void* Vcur,
                               void* Vout1, void* Vout2, int64_t s0, double2* acc, const double* am,
                               const double* ao, int m, cudaStream_t s);
-// batched FP32 step over ncell cells of one shape (plan p, full-width slabs)
+// batched FP32 step over ncell cells of one shape (plan p, full-width slabs);
+// with p.tma_rows > 0 and `maps` (device copy of the 2 ncell tensor maps that
+// encode_batch_maps writes to host memory, batch_maps_bytes(ncell) bytes,
+// 64-byte aligned) the TMA-staged kernel runs, else the cp.async one
 cudaError_t cheb_prepare_batched(const ChebPlan& p);
+size_t batch_maps_bytes(int ncell);
+cudaError_t encode_batch_maps(const ChebPlan& p, int ncell, const BatchPtrs& b, void* host_maps);
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
-                                     cudaStream_t s);
+                                     cudaStream_t s, const void* maps = nullptr);
 // table conj(xi_J) of the probing phases, J < D
 cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s);
 // acc += a_m V[local rows] for the slab's columns (no recursion)
