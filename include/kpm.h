@@ -49,7 +49,7 @@ extern "C" {
 #define KPM_ENOMEM (-2)      /* scratch allocation failed */
 #define KPM_ECUDA (-3)       /* a CUDA call failed; kpm_last_error() has the CUDA message */
 #define KPM_ENONFINITE (-4)  /* NaN or Inf in an output */
-#define KPM_ETIMEDOUT (-5)   /* a bounded device wait expired (reserved; no kernel of this library spins) */
+#define KPM_ETIMEDOUT (-5)   /* reserved: no call returns it (device waits that expire poison outputs, below) */
 #define KPM_ENOTCONV (-6)    /* rmft_iterate reached n_iter without meeting tol (only if asked to report it) */
 
 #define KPM_FP64 0
@@ -173,7 +173,13 @@ int kpm_bounds(kpm_ctx* ctx, const kpm_model* model, const double* fields,
  * F_M = sum_m (2 - delta_m0) g_m c_m T_m the Jackson-damped T = 0 step at BdG
  * energy 0; omega = a tr G_M(h~) with G_M the damped series of min(x - x0, 0).
  * fields, ab: device (ab as written by kpm_bounds).  obs: device 26*N,
- * written.  omega: device double or NULL. */
+ * written.  omega: device double or NULL.
+ * Asynchronous on `stream`.  The FP32 recursion moves its rows by TMA copies
+ * that complete on mbarriers; its waits are bounded in time (2 s), and a
+ * recursion whose copies never land writes NaN over the rows it owns (and
+ * every later FP32 recursion launch of the process does the same), so such a
+ * device failure shows as NaN in obs (KPM_ENONFINITE from rmft_iterate)
+ * rather than as a hang. */
 int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                     const double* fields, const double* ab, double* obs,
                     double* omega, void* stream);
