@@ -1,12 +1,14 @@
 """Model check of the ring protocol of the TMA-staged FP32 recursion step.
 
-The kernel keeps lattice rows y-1..y+1 of V_m in a 5-slot ring and the 2h~
-entries of row y in a 3-slot ring, each slot completing on its own mbarrier
-(one arrival with the expected byte count, then the copy's bytes), and has no
-block barrier: every warp arrives on a row-done mbarrier (ring of three,
-count = warps) when it has finished a row, and the issuing thread waits for
-row y-1 to be done before it refills the window slot of row y-2 (with row
-y+3) and the coefficient slot of row y-1 (with row y+2).  Waits test only the
+The kernel keeps lattice rows y-1..y+1 of V_m (and the next rows in flight)
+in a ring of VR slots and the 2h~ entries of row y in a ring of CR slots, each
+slot completing on its own mbarrier (one arrival with the expected byte
+count, then the copy's bytes), and has no block barrier: every warp arrives
+on a row-done mbarrier (ring of DR, count = warps) when it has finished a
+row, and the issuing thread waits for row y-1 to be done before it refills
+the window slot of row y-2 (with row y+VR-3) and the coefficient slot of row
+y-1 (with row y+CR-2).  The kernel uses VR, CR, DR = 5, 3, 3; a deeper
+window ring (6, 3, 4) is checked too.  Waits test only the
 parity of a phase, so the protocol must never let a barrier run two phases
 ahead of a waiter, must never re-arm a slot whose copy is in flight, and must
 never overwrite a slot a warp still reads.  This test replays the protocol
@@ -30,13 +32,13 @@ class _Bar:
         return (self.phase & 1) != parity
 
 
-def _run(nrow, warps, seed):
+def _run(nrow, warps, seed, VR=5, CR=3, DR=3):
     rng = random.Random(seed)
-    fv = [_Bar(1) for _ in range(5)]
-    fc = [_Bar(1) for _ in range(3)]
-    dn = [_Bar(warps) for _ in range(3)]
-    vslot = [None] * 5
-    cslot = [None] * 3
+    fv = [_Bar(1) for _ in range(VR)]
+    fc = [_Bar(1) for _ in range(CR)]
+    dn = [_Bar(warps) for _ in range(DR)]
+    vslot = [None] * VR
+    cslot = [None] * CR
     flight = []
 
     def issue(bars, slots, ring, kind, idx):
@@ -47,10 +49,10 @@ def _run(nrow, warps, seed):
         slots[idx % ring] = ("in flight", idx)
         flight.append((b, slots, idx % ring, idx))
 
-    for w in range(0, min(3, nrow + 1) + 1):
-        issue(fv, vslot, 5, "window", w)
-    for c in range(0, min(1, nrow - 1) + 1):
-        issue(fc, cslot, 3, "coefficient", c)
+    for w in range(0, min(VR - 2, nrow + 1) + 1):
+        issue(fv, vslot, VR, "window", w)
+    for c in range(0, min(CR - 2, nrow - 1) + 1):
+        issue(fc, cslot, CR, "coefficient", c)
     state = [[0, "wait"] for _ in range(warps)]
     for _ in range(10 ** 6):
         live = [i for i, (q, _) in enumerate(state) if q < nrow]
@@ -68,27 +70,27 @@ def _run(nrow, warps, seed):
         q, st = state[i]
         if st == "wait":
             ok = q > 0 or (fv[0].done(0) and fv[1].done(0))
-            ok = ok and fv[(q + 2) % 5].done(((q + 2) // 5) & 1) and fc[q % 3].done((q // 3) & 1)
+            ok = ok and fv[(q + 2) % VR].done(((q + 2) // VR) & 1) and fc[q % CR].done((q // CR) & 1)
             if ok:
                 state[i][1] = "issue" if i == 0 else "compute"
         elif st == "issue":
-            if q >= 1 and not dn[(q - 1) % 3].done(((q - 1) // 3) & 1):
+            if q >= 1 and not dn[(q - 1) % DR].done(((q - 1) // DR) & 1):
                 continue
-            if q + 4 <= nrow + 1:
-                issue(fv, vslot, 5, "window", q + 4)
-            if q + 2 < nrow:
-                issue(fc, cslot, 3, "coefficient", q + 2)
+            if q + VR - 1 <= nrow + 1:
+                issue(fv, vslot, VR, "window", q + VR - 1)
+            if q + CR - 1 < nrow:
+                issue(fc, cslot, CR, "coefficient", q + CR - 1)
             state[i][1] = "compute"
         elif st == "compute":
             for w in (q, q + 1, q + 2):
-                assert vslot[w % 5] == ("ok", w), (q, w, vslot[w % 5])
-            assert cslot[q % 3] == ("ok", q)
+                assert vslot[w % VR] == ("ok", w), (q, w, vslot[w % VR])
+            assert cslot[q % CR] == ("ok", q)
             state[i][1] = "arrive"
         else:  # the reads of the row are over only now: nothing may have replaced them
             for w in (q, q + 1, q + 2):
-                assert vslot[w % 5] == ("ok", w), ("overwritten", q, w)
-            assert cslot[q % 3] == ("ok", q)
-            b = dn[q % 3]
+                assert vslot[w % VR] == ("ok", w), ("overwritten", q, w)
+            assert cslot[q % CR] == ("ok", q)
+            b = dn[q % DR]
             b.pending -= 1
             if b.pending == 0:
                 b.phase += 1
@@ -97,8 +99,16 @@ def _run(nrow, warps, seed):
     raise AssertionError("no progress: the protocol deadlocks")
 
 
+@pytest.mark.parametrize("rings", [(5, 3, 3), (6, 3, 4)])
 @pytest.mark.parametrize("nrow", [1, 2, 3, 5, 7, 34])
 @pytest.mark.parametrize("warps", [1, 2, 16])
-def test_ring_protocol_random_schedules(nrow, warps):
+def test_ring_protocol_random_schedules(rings, nrow, warps):
     for seed in range(12):
-        _run(nrow, warps, seed)
+        _run(nrow, warps, seed, *rings)
+
+
+def test_too_short_done_ring_is_caught():
+    # warps may run CR - 1 rows apart: a row-done ring of CR - 1 phases aliases
+    with pytest.raises(AssertionError):
+        for seed in range(50):
+            _run(34, 4, seed, 5, 3, 2)
