@@ -49,7 +49,7 @@ extern "C" {
 #define KPM_ENOMEM (-2)      /* scratch allocation failed */
 #define KPM_ECUDA (-3)       /* a CUDA call failed; kpm_last_error() has the CUDA message */
 #define KPM_ENONFINITE (-4)  /* NaN or Inf in an output */
-#define KPM_ETIMEDOUT (-5)   /* reserved: no call returns it (device waits that expire poison outputs, below) */
+#define KPM_ETIMEDOUT (-5)   /* a bounded device wait of the FP32 recursion expired (kpm_sync_status, rmft_iterate) */
 #define KPM_ENOTCONV (-6)    /* rmft_iterate reached n_iter without meeting tol (only if asked to report it) */
 
 #define KPM_FP64 0
@@ -142,6 +142,15 @@ int kpm_create(kpm_ctx** out, int device);
 int kpm_destroy(kpm_ctx* ctx);
 /* Upper bound (bytes) on recursion-slab scratch; default 24 GiB. */
 int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes);
+/* Synchronise `stream` (NULL: the legacy default stream) and read the device
+ * fault word of the FP32 recursion: KPM_OK; KPM_ETIMEDOUT when one of its
+ * bounded waits for its own TMA copies expired (that launch and every later
+ * FP32 recursion launch of the process wrote NaN instead of results; the word
+ * is never cleared); KPM_ECUDA for an asynchronous CUDA error or a recursion
+ * that found its shared memory misaligned for TMA (outputs NaN as well).
+ * rmft_iterate and rmft_iterate_batched read the word themselves when an
+ * iteration turns non-finite. */
+int kpm_sync_status(kpm_ctx* ctx, void* stream);
 const char* kpm_strerror(int status);
 /* Last error message of this context (static storage of the context). */
 const char* kpm_last_error(const kpm_ctx* ctx);
@@ -178,8 +187,8 @@ int kpm_bounds(kpm_ctx* ctx, const kpm_model* model, const double* fields,
  * that complete on mbarriers; its waits are bounded in time (2 s), and a
  * recursion whose copies never land writes NaN over the rows it owns (and
  * every later FP32 recursion launch of the process does the same), so such a
- * device failure shows as NaN in obs (KPM_ENONFINITE from rmft_iterate)
- * rather than as a hang. */
+ * device failure shows as NaN in obs and as KPM_ETIMEDOUT from
+ * kpm_sync_status and rmft_iterate, rather than as a hang. */
 int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                     const double* fields, const double* ab, double* obs,
                     double* omega, void* stream);

@@ -1560,6 +1560,10 @@ cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPt
   return cudaErrorInvalidValue;
 }
 
+cudaError_t read_step_fault(unsigned int* out) {
+  return cudaMemcpyFromSymbol(out, g_step_fault, sizeof(unsigned int));
+}
+
 cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((p.D + 255) / 256, 4 * kSMs));
   probe_phase_kernel<<<grid, 256, 0, s>>>(p.D, p.probe_seed, xi_conj);

@@ -477,6 +477,27 @@ int kpm_destroy(kpm_ctx* ctx) {
   return KPM_OK;
 }
 
+// KPM_ETIMEDOUT / KPM_ECUDA for a fault recorded by the FP32 recursion, else 0
+static int device_fault_status(kpm_ctx* ctx) {
+  unsigned int f = 0;
+  const cudaError_t e = read_step_fault(&f);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device fault word");
+  if (f & 1u)
+    return fail(ctx, KPM_ETIMEDOUT,
+                "a bounded wait of the FP32 recursion expired: its outputs and those of every later FP32 recursion "
+                "launch in this process are NaN");
+  if (f & 2u)
+    return fail(ctx, KPM_ECUDA, "shared memory of the FP32 recursion was not aligned for TMA: outputs are NaN");
+  return KPM_OK;
+}
+
+int kpm_sync_status(kpm_ctx* ctx, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  DeviceGuard g(ctx->device);
+  KPM_CU(cudaStreamSynchronize((cudaStream_t)stream));
+  return device_fault_status(ctx);
+}
+
 int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes) {
   if (!ctx || bytes < (1u << 20)) return KPM_EINVAL;
   ctx->budget = bytes;
@@ -660,7 +681,8 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     st.density_error = h[5];
     st.iterations = it + 1;
     if (!(st.residual == st.residual) || !(st.omega == st.omega) || st.residual > 1e300) {
-      status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in the RMFT iteration");
+      status = device_fault_status(ctx);
+      if (status == KPM_OK) status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in the RMFT iteration");
       break;
     }
     st.converged = st.residual < ropts->tol && fabs(st.density_error) < ropts->tol;
@@ -1121,8 +1143,10 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       q.residual = h[4];
       q.density_error = h[5];
       q.iterations = it + 1;
-      if (!(q.residual == q.residual) || !(q.omega == q.omega) || q.residual > 1e300)
-        status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in a batched cell");
+      if (!(q.residual == q.residual) || !(q.omega == q.omega) || q.residual > 1e300) {
+        status = device_fault_status(ctx);
+        if (status == KPM_OK) status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in a batched cell");
+      }
       q.converged = q.residual < ropts[c].tol && fabs(q.density_error) < ropts[c].tol;
       all = all && q.converged;
     }

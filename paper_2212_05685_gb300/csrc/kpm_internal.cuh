@@ -126,6 +126,9 @@ size_t batch_maps_bytes(int ncell);
 cudaError_t encode_batch_maps(const ChebPlan& p, int ncell, const BatchPtrs& b, void* host_maps);
 cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPtrs& b, int m, int mode,
                                      cudaStream_t s, const void* maps = nullptr);
+// device fault word of the TMA-staged FP32 step (bit 0: a bounded wait
+// expired; bit 1: shared memory misaligned for TMA); sticky for the process
+cudaError_t read_step_fault(unsigned int* out);
 // table conj(xi_J) of the probing phases, J < D
 cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s);
 // acc += a_m V[local rows] for the slab's columns (no recursion)

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "kpm_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "kpm_destroy": (ctypes.c_int, [_P]),
     "kpm_set_scratch_budget": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "kpm_sync_status": (ctypes.c_int, [_P, _P]),
     "kpm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kpm_last_error": (ctypes.c_char_p, [_P]),
     "kpm_peierls_phases": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), _P, _P]),
@@ -185,6 +186,10 @@ def kpm_destroy(ctx: Context):
 
 def kpm_set_scratch_budget(ctx: Context, nbytes: int):
     return ctx.check(ctx.lib.kpm_set_scratch_budget(ctx.handle, int(nbytes)), "kpm_set_scratch_budget")
+
+
+def kpm_sync_status(ctx: Context, stream=None):
+    return ctx.check(ctx.lib.kpm_sync_status(ctx.handle, _stream(stream)), "kpm_sync_status")
 
 
 def kpm_peierls_phases(ctx: Context, model, phi, stream=None):
