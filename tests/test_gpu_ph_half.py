@@ -143,3 +143,33 @@ def test_half_pass_refused_outside_the_sector(K):
         kpm.kpm_backward(ctx, model, half, fields, ab, g, 0.0, gf)
     obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
     assert kpm.kpm_observables_noalloc(model, half, fields, ab, obs) == kpm.KPM_EINVAL
+
+
+def test_full_size_half_pass_sampled_sites(K):
+    """100 x 100 two-vortex cell with the PDW seed, M = 2048, FP32, half pass
+    as benchmarked: sites sampled across the lattice against the oracle's
+    recursion on both of their columns (the oracle propagates the (j, dn)
+    columns the GPU reconstructs from the particle-hole relation)."""
+    kpm, _ = K
+    w = inputs.CFG2
+    nx, ny, N = w.nx, w.ny, w.n_sites
+    p = inputs.vortex_seed(w)
+    model, phi, fields, ab = _fields(K, nx, ny, p, 0.0)
+    st, half, _ = _pass(K, model, fields, ab, w.M, kpm.KPM_FP32, kpm.KPM_FLAG_PH_HALF)
+    assert st == kpm.KPM_OK
+    orm = rmft.Model(nx, ny)
+    f = rmft.fields(orm, p, 0.0)
+    a, b = bdg.gershgorin(orm, f)
+    assert ab.cpu().numpy() == pytest.approx([a, b], rel=1e-13, abs=1e-14)
+    rng = np.random.default_rng(11)
+    sites = np.concatenate([[0, nx - 1, N - 1, 25 + 50 * nx, 75 + 50 * nx], rng.choice(N, 3, replace=False)])
+    cols = np.sort(np.concatenate([2 * sites, 2 * sites + 1]))
+    Fc, _ = okpm.f_naive(bdg.csr(orm, f), a, b, w.M, cols=cols)
+    full = np.zeros((2 * N, 2 * N), dtype=np.complex128, order="F")
+    full[:, cols] = Fc
+    ref = okpm.observables(orm, full)
+    gn, gc, gF = rmft.split(half, N)
+    rn, rc, rF = rmft.split(ref, N)
+    assert np.max(np.abs(gn[:, sites] - rn[:, sites])) < 2e-5
+    assert np.max(np.abs(gc[:, :, sites] - rc[:, :, sites])) < 2e-5
+    assert np.max(np.abs(gF[:, sites] - rF[:, sites])) < 2e-5
