@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-ph-half", action="store_true", help="skip the particle-hole half-pass section")
     ap.add_argument("--no-probing", action="store_true", help="skip the probing-estimator section")
     ap.add_argument("--no-ldos", action="store_true", help="skip the LDOS section")
+    ap.add_argument("--no-df64", action="store_true", help="skip the double-float recursion section")
     ap.add_argument("--double-step", action="store_true",
                     help="FP32 recursion two steps per launch (default: as the autotuner chooses, else one)")
     ap.add_argument("--profile-probing", action="store_true",
@@ -416,6 +417,32 @@ def run_ours(args):
                 "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
                 "fp32_speedup": t64 / (t / args.steps)}
 
+    # double-float recursion (FP64-accurate, FP32 pipes) at M = 128, scaled
+    # to M = 2048 like the FP64 line; its error against FP64 is in fp32_error
+    df64 = None
+    if not args.no_df64:
+        Ms = 128
+        fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        ab = torch.empty(2, dtype=torch.float64, device="cuda")
+        obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+        kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+        odf = kpm.make_opts(Ms, kpm.KPM_DF64)
+        kpm.kpm_observables(ctx, model, odf, fields, ab, obs)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        kpm.kpm_observables(ctx, model, odf, fields, ab, obs)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        tdf = a0.elapsed_time(a1) / 1e3 * (M - 1) / (Ms - 1)
+        df64 = {"s_per_pass": tdf, "vector_moments_per_s": D * M / tdf,
+                "fp64_equivalent_tflops": 106.0 * D * D * (M - 1) / tdf / 1e12,
+                "fp64_nominal_tflops": 1.25,
+                "speedup_vs_fp64": (fp64["s_per_pass"] / tdf) if fp64 else None,
+                "sample": f"double-float pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)"}
+
     # particle-hole half pass on the same cell (paramagnetic singlet sector:
     # n_up = n_dn, chi_up = chi_dn, F_ij = F_ji hold for the seed and are kept)
     ph_half = None
@@ -488,6 +515,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "fp64": fp64,
+        "df64": df64,
         "fp32_error": precision,
         "ph_half": ph_half,
         "probing": probe,
@@ -641,15 +669,17 @@ def precision_section(kpm, inputs, torch):
     ab = torch.empty(2, dtype=torch.float64, device="cuda")
     kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
     out = {}
-    for name, prec in (("fp64", kpm.KPM_FP64), ("fp32", kpm.KPM_FP32)):
+    for name, prec in (("fp64", kpm.KPM_FP64), ("fp32", kpm.KPM_FP32), ("df64", kpm.KPM_DF64)):
         obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
         kpm.kpm_observables(ctx, model, kpm.make_opts(w.M, prec), fields, ab, obs)
         out[name] = obs
     torch.cuda.synchronize()
     d = (out["fp32"] - out["fp64"]).abs()
+    e = (out["df64"] - out["fp64"]).abs()
     kpm.kpm_destroy(ctx)
     return {"cell": "48x24", "M": w.M, "max_err_n": float(d[:2 * N].max()), "max_err_chi": float(d[2 * N:18 * N].max()),
-            "max_err_F": float(d[18 * N:].max()), "bound": 2e-5}
+            "max_err_F": float(d[18 * N:].max()), "bound": 2e-5,
+            "df64_max_err": float(e.max()), "df64_bound": 1e-10}
 
 
 def adjoint_section(kpm, inputs, torch):

@@ -54,6 +54,7 @@ extern "C" {
 
 #define KPM_FP64 0
 #define KPM_FP32 1
+#define KPM_DF64 2  /* double-float: FP64-accurate recursion in FP32 hi + lo pairs */
 
 typedef struct kpm_ctx kpm_ctx;
 
@@ -70,7 +71,13 @@ typedef struct {
 typedef struct {
   int32_t M;            /* number of moments, M >= 1 (paper: 1000-2000) */
   int32_t precision;    /* KPM_FP64: FP64 recursion; KPM_FP32: FP32 vectors and
-                           coefficients, FP64 moment sums and everything else */
+                           coefficients, FP64 moment sums and everything else;
+                           KPM_DF64: vectors and coefficients as double-float
+                           (hi + lo FP32 pairs, about 48 bits), arithmetic on the
+                           FP32 pipes, FP64 everything else (kpm_observables,
+                           rmft_iterate, kpm_autotune; refused with KPM_EINVAL by
+                           kpm_backward, kpm_ldos, rmft_iterate_batched and
+                           kpm_observables_noalloc) */
   int32_t block_width;  /* unit start vectors per slab; 0 = as many as fit the
                            context's scratch budget (kpm_set_scratch_budget) */
   int32_t cols_per_block; /* columns per CTA in the recursion kernel; 0 = default */

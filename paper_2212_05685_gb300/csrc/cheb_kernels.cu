@@ -71,6 +71,76 @@ template <typename V>
 __device__ __forceinline__ V vzero();
 template <>
 __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 vhalf(double2 v) { return vscale(v, 0.5); }
+__device__ __forceinline__ void vfinish(double2&) {}
+// the two real diagonals packed in table entry 0, and an element as FP64
+__device__ __forceinline__ double diag0(double2 d) { return d.x; }
+__device__ __forceinline__ double diag1(double2 d) { return d.y; }
+__device__ __forceinline__ double cre(double2 v) { return v.x; }
+__device__ __forceinline__ double cim(double2 v) { return v.y; }
+
+// Double-float (KPM_DF64): every real is the unevaluated sum hi + lo of two
+// FP32 numbers, about 48 significant bits, so the FP64-accurate recursion runs
+// on the FP32 pipes.  A complex element is float4 (re_hi, re_lo, im_hi, im_lo);
+// table entry 0 holds the two real diagonals as (d0_hi, d0_lo, d1_hi, d1_lo).
+// Products use the exact FMA residual of hi * hi (p + e = xh yh exactly) plus
+// the cross terms; sums use Knuth's two-sum, whose error term is exact for any
+// ordering of the operands; an accumulator is renormalised once per output.
+struct DF {};
+template <>
+struct CT<DF> {
+  using C = float4;
+  using V = float4;
+  static constexpr int VW = 1;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (h, l) += (xh + xl)(yh + yl), dropping xl yl (below 2^-48 of the product)
+__device__ __forceinline__ void df_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -p);
+  e = __fmaf_rn(xh, yl, e);
+  e = __fmaf_rn(xl, yh, e);
+  float s, t;
+  two_sum(h, p, s, t);
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(t, e));
+}
+__device__ __forceinline__ void cmac(float4& a, float4 c, float4 v) {
+  df_mac(a.x, a.y, c.x, c.y, v.x, v.y);
+  df_mac(a.x, a.y, -c.z, -c.w, v.z, v.w);
+  df_mac(a.z, a.w, c.x, c.y, v.z, v.w);
+  df_mac(a.z, a.w, c.z, c.w, v.x, v.y);
+}
+__device__ __forceinline__ void rmac(float4& a, float2 d, float4 v) {
+  df_mac(a.x, a.y, d.x, d.y, v.x, v.y);
+  df_mac(a.z, a.w, d.x, d.y, v.z, v.w);
+}
+__device__ __forceinline__ float4 vneg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ float4 vhalf(float4 v) { return make_float4(0.5f * v.x, 0.5f * v.y, 0.5f * v.z, 0.5f * v.w); }
+template <>
+__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vfinish(float4& v) {
+  float h, l;
+  two_sum(v.x, v.y, h, l);
+  v.x = h;
+  v.y = l;
+  two_sum(v.z, v.w, h, l);
+  v.z = h;
+  v.w = l;
+}
+__device__ __forceinline__ float2 diag0(float4 d) { return make_float2(d.x, d.y); }
+__device__ __forceinline__ float2 diag1(float4 d) { return make_float2(d.z, d.w); }
+__device__ __forceinline__ double cre(float4 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double cim(float4 v) { return (double)v.z + (double)v.w; }
+// FP64 value as hi + lo (the rounding residual of hi is exact in FP64)
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -221,7 +291,6 @@ __global__ void __launch_bounds__(512, 1)
   }
   cp_commit();
 
-  const Real half = (Real)0.5;
   for (int q = 0; q < nrow; ++q) {
     const int y = y0 + q;
     cp_wait_1();
@@ -250,8 +319,8 @@ __global__ void __launch_bounds__(512, 1)
       const C* cf = cf_row + x * kCoef;
       {
         const C d = cf[0];
-        rmac(a0, d.x, KPM_LD(w0, x, 0));
-        rmac(a1, d.y, KPM_LD(w0, x, 1));
+        rmac(a0, diag0(d), KPM_LD(w0, x, 0));
+        rmac(a1, diag1(d), KPM_LD(w0, x, 1));
       }
       // neighbours k = 1..8: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1)
       const C* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
@@ -269,9 +338,11 @@ __global__ void __launch_bounds__(512, 1)
       }
 #undef KPM_LD
       if (MODE == 0) {
-        a0 = vscale(a0, half);
-        a1 = vscale(a1, half);
+        a0 = vhalf(a0);
+        a1 = vhalf(a1);
       }
+      vfinish(a0);
+      vfinish(a1);
       *reinterpret_cast<V*>(Vout + g0) = a0;
       *reinterpret_cast<V*>(Vout + g0 + ldv) = a1;
     }
@@ -293,8 +364,8 @@ __global__ void __launch_bounds__(512, 1)
         const C* w = dy < 0 ? wm : (dy > 0 ? wp : w0);
         const int al = kSlotFlip[s] ? 1 - beta : beta;
         const C val = w[(2 * xs + al) * CB + c];
-        acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
-        if (s == 0 && cmap.rec) record_diag(cmap, D, m, J, wgt, (double)val.x, (double)val.y);
+        acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, cre(val), cim(val));
+        if (s == 0 && cmap.rec) record_diag(cmap, D, m, J, wgt, cre(val), cim(val));
       }
     }
     __syncthreads();
@@ -1104,6 +1175,16 @@ __global__ void cheb_init_f64_kernel(int64_t D, int64_t ldv, int nx, double2* __
     V0[k] = start_entry(K, c, D, nx, cm);
   }
 }
+// double-float layout: float4 (re_hi, re_lo, im_hi, im_lo)
+__global__ void cheb_init_df_kernel(int64_t D, int64_t ldv, int nx, float4* __restrict__ V0, ColMap cm) {
+  const int64_t total = D * ldv;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t K = k / ldv, c = k - K * ldv;
+    const double2 e = start_entry(K, c, D, nx, cm);
+    const float2 re = df_split(e.x), im = df_split(e.y);
+    V0[k] = make_float4(re.x, re.y, im.x, im.y);
+  }
+}
 // FP32 pair-split layout: float4 (re_2p, re_2p+1, im_2p, im_2p+1)
 __global__ void cheb_init_f32_kernel(int64_t D, int64_t ldv, int nx, float4* __restrict__ V0, ColMap cm) {
   const int64_t ldq = ldv / 2;
@@ -1149,7 +1230,8 @@ __global__ void probe_phase_kernel(int64_t D, uint32_t seed, double2* __restrict
 }
 
 // acc += a_m V[local rows] (the last moment, which no step reads again)
-template <bool F32>
+// LAY: 0 FP64 interleaved complex, 1 FP32 pair-split, 2 double-float
+template <int LAY>
 __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64_t width, const void* __restrict__ V,
                                    ColMap cm, double2* __restrict__ acc, const double* __restrict__ am,
                                    const double* __restrict__ ao, int m) {
@@ -1176,10 +1258,14 @@ __global__ void cheb_gather_kernel(int nx, int ny, int64_t D, int64_t ldv, int64
     const int al = kSlotFlip[s] ? 1 - beta : beta;
     const int64_t K = 2 * ((int64_t)ys * nx + xs) + al;
     double re, im;
-    if (F32) {
+    if (LAY == 1) {
       const float2 val = pair_elem(reinterpret_cast<const float4*>(V) + K * (ldv / 2), (int)c);
       re = val.x;
       im = val.y;
+    } else if (LAY == 2) {
+      const float4 val = reinterpret_cast<const float4*>(V)[K * ldv + c];
+      re = cre(val);
+      im = cim(val);
     } else {
       const double2 val = reinterpret_cast<const double2*>(V)[K * ldv + c];
       re = val.x;
@@ -1331,6 +1417,29 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
   return cudaGetLastError();
 }
 template <int CB>
+cudaError_t set_smem_df(int nx) {
+  cudaError_t e = cudaFuncSetAttribute(cheb_step_kernel<DF, CB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemLimit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cheb_step_kernel<DF, CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSmemLimit);
+}
+template <int CB>
+cudaError_t launch_df(const ChebPlan& p, const void* table, const void* Vcur, const void* Vprev, void* Vout,
+                      int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
+  const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
+  if (mode == 0)
+    cheb_step_kernel<DF, CB, 0><<<grid, p.nthreads, p.smem, s>>>(
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const float4*)table, (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
+        colmap(p, s0), acc, am, ao, m);
+  else
+    cheb_step_kernel<DF, CB, 1><<<grid, p.nthreads, p.smem, s>>>(
+        p.nx, p.ny, p.D, p.ldv, p.ylen, (const float4*)table, (const float4*)Vcur, (const float4*)Vprev, (float4*)Vout,
+        colmap(p, s0), acc, am, ao, m);
+  return cudaGetLastError();
+}
+
+template <int CB>
 cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, const void* Vprev, void* Vout,
                        int64_t s0, double2* acc, const double* am, const double* ao, int m, int mode, cudaStream_t s) {
   const dim3 grid((p.ny + p.ylen - 1) / p.ylen, (unsigned)(p.ldv / CB));
@@ -1457,6 +1566,13 @@ cudaError_t cheb_prepare(const ChebPlan& p, int precision) {
       case 4: return set_smem_f32<4>(p.nx);
       case 2: return set_smem_f32<2>(p.nx);
     }
+  } else if (precision == KPM_DF64) {
+    switch (p.cb) {
+      case 8: return set_smem_df<8>(p.nx);
+      case 4: return set_smem_df<4>(p.nx);
+      case 2: return set_smem_df<2>(p.nx);
+      case 1: return set_smem_df<1>(p.nx);
+    }
   } else {
     switch (p.cb) {
       case 8: return set_smem_f64<8>(p.nx);
@@ -1474,6 +1590,8 @@ cudaError_t launch_cheb_init(const ChebPlan& p, int precision, void* V0, int64_t
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 8 * kSMs * 4);
   if (precision == KPM_FP32)
     cheb_init_f32_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, p.nx, (float4*)V0, colmap(p, s0));
+  else if (precision == KPM_DF64)
+    cheb_init_df_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, p.nx, (float4*)V0, colmap(p, s0));
   else
     cheb_init_f64_kernel<<<grid, 256, 0, s>>>(p.D, p.ldv, p.nx, (double2*)V0, colmap(p, s0));
   cudaError_t e = cudaGetLastError();
@@ -1493,6 +1611,13 @@ cudaError_t launch_cheb_step(const ChebPlan& p, int precision, const void* table
       case 8: return launch_f32<8>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
       case 4: return launch_f32<4>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
       case 2: return launch_f32<2>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+    }
+  } else if (precision == KPM_DF64) {
+    switch (p.cb) {
+      case 8: return launch_df<8>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 4: return launch_df<4>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 2: return launch_df<2>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
+      case 1: return launch_df<1>(p, table, Vcur, Vprev, Vout, s0, acc, am, ao, m, mode, s);
     }
   } else {
     switch (p.cb) {
@@ -1575,10 +1700,11 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
   const int64_t width = p.ldv;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((width * kSlots + 255) / 256, 4 * kSMs));
   if (precision == KPM_FP32)
-    cheb_gather_kernel<true><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao, m);
+    cheb_gather_kernel<1><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao, m);
+  else if (precision == KPM_DF64)
+    cheb_gather_kernel<2><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao, m);
   else
-    cheb_gather_kernel<false><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao,
-                                                   m);
+    cheb_gather_kernel<0><<<grid, 256, 0, s>>>(p.nx, p.ny, p.D, p.ldv, width, V, colmap(p, s0), acc, am, ao, m);
   return cudaGetLastError();
 }
 

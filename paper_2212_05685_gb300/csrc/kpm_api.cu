@@ -201,7 +201,8 @@ int64_t balanced_width(int64_t D, int64_t width) {
 int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp) {
   if (!o) return fail(ctx, KPM_EINVAL, "opts is null");
   if (o->M < 1) return fail(ctx, KPM_EINVAL, "M must be >= 1");
-  if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return fail(ctx, KPM_EINVAL, "unknown precision");
+  if (o->precision != KPM_FP32 && o->precision != KPM_FP64 && o->precision != KPM_DF64)
+    return fail(ctx, KPM_EINVAL, "unknown precision");
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
@@ -312,6 +313,8 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js, o->temperature));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
+  else if (prec == KPM_DF64)
+    KPM_CU(launch_scale_table_df(*m, fields, ab, (float4*)ctx->table, s));
   else
     KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
   nl += 2;
@@ -718,6 +721,7 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int K = M >= 2 ? (M - 1 + seg - 1) / seg : 0;  // segments, each serving m in [k seg + 1, (k+1) seg]
   const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
 
+  if (opts->precision == KPM_DF64) return fail(ctx, KPM_EINVAL, "KPM_DF64: not supported by kpm_backward");
   if (opts && (opts->flags & KPM_FLAG_PH_HALF)) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by kpm_backward");
   if (opts && opts->probe_p) return fail(ctx, KPM_EINVAL, "probing: not supported by kpm_backward");
   // slab width from the budget over all adjoint slab vectors (plus the forward pair);
@@ -840,6 +844,7 @@ int kpm_ldos(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const d
   if (!opts || !omega || n_omega < 1) return fail(ctx, KPM_EINVAL, "bad LDOS arguments");
   if (!(gamma0 > 0.0) || !(gamma_alpha >= 0.0)) return fail(ctx, KPM_EINVAL, "need gamma0 > 0 and gamma_alpha >= 0");
   if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: the LDOS needs both Nambu rows");
+  if (opts->precision == KPM_DF64) return fail(ctx, KPM_EINVAL, "KPM_DF64: not supported by kpm_ldos");
   DeviceGuard g(ctx->device);
   const int N = model->nx * model->ny;
   const int64_t D = 2 * (int64_t)N;

@@ -85,6 +85,9 @@ cudaError_t launch_coefficients(int M, const double* ab, double* am, double* ao,
 // per-site table of 2h~ entries in precision T (kCoef complex per site)
 cudaError_t launch_scale_table_f32(const kpm_model& m, const double* fields, const double* ab,
                                    float2* table, cudaStream_t s);
+// double-float table: entries as float4 (re_hi, re_lo, im_hi, im_lo)
+cudaError_t launch_scale_table_df(const kpm_model& m, const double* fields, const double* ab, float4* table,
+                                  cudaStream_t s);
 cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, const double* ab,
                                    double2* table, cudaStream_t s);
 // obs from accumulators; omega = a * sum Re acc[J][9] (if omega != null)

@@ -468,6 +468,12 @@ template <>
 __device__ __forceinline__ float2 to_c<float2>(Cplx v) { return make_float2((float)v.re, (float)v.im); }
 template <>
 __device__ __forceinline__ double2 to_c<double2>(Cplx v) { return make_double2(v.re, v.im); }
+// double-float: each FP64 part as hi + lo with lo the rounding residual of hi
+template <>
+__device__ __forceinline__ float4 to_c<float4>(Cplx v) {
+  const float rh = __double2float_rn(v.re), ih = __double2float_rn(v.im);
+  return make_float4(rh, __double2float_rn(v.re - (double)rh), ih, __double2float_rn(v.im - (double)ih));
+}
 
 
 template <typename C>
@@ -812,6 +818,13 @@ cudaError_t launch_scale_table_f32(const kpm_model& m, const double* fields, con
                                    cudaStream_t s) {
   const int N = m.nx * m.ny;
   scale_table_kernel<float2><<<(N + 127) / 128, 128, 0, s>>>(m, fields, ab, table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_table_df(const kpm_model& m, const double* fields, const double* ab, float4* table,
+                                  cudaStream_t s) {
+  const int N = m.nx * m.ny;
+  scale_table_kernel<float4><<<(N + 127) / 128, 128, 0, s>>>(m, fields, ab, table);
   return cudaGetLastError();
 }
 

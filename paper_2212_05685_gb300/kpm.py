@@ -23,6 +23,7 @@ KPM_ETIMEDOUT = -5
 KPM_ENOTCONV = -6
 KPM_FP64 = 0
 KPM_FP32 = 1
+KPM_DF64 = 2
 KPM_FLAG_DOUBLE_STEP = 1
 KPM_FLAG_PH_HALF = 2
 
