@@ -14,9 +14,12 @@
 //
 // Layout: V is row-major, V[K][c] with K = 2 i + alpha the Nambu row and c the
 // column inside the slab; the row stride ldv is the slab width rounded up to
-// the CTA's column chunk.  FP64 stores interleaved complex (re, im).  FP32
-// stores each column pair (2p, 2p+1) as (re_2p, re_2p+1, im_2p, im_2p+1) so
-// that one packed f32x2 FMA advances two columns.  h~ is a 13-point stencil
+// the CTA's column chunk.  FP64 stores interleaved complex (re, im);
+// double-float (KPM_DF64) stores (re_hi, re_lo, im_hi, im_lo), each real the
+// unevaluated FP32 sum hi + lo, and runs the FP64 kernel's structure with
+// double-float arithmetic.  FP32 stores each column pair (2p, 2p+1) as
+// (re_2p, re_2p+1, im_2p, im_2p+1) so that one packed f32x2 FMA advances two
+// columns.  h~ is a 13-point stencil
 // per row (diagonal, eight hops, four pairings), read from a per-site table
 // of kCoef complex 2h~ entries.
 //
