@@ -196,3 +196,27 @@ def observables(model, Fmat):
 def observables_from_columns(model, cols_mat):
     """Same as `observables` when cols_mat holds all D columns of f(h)."""
     return observables(model, cols_mat)
+
+
+def observables_at(model, Fc, cols, sites):
+    """Order parameters of `sites` (readings N2, N3) from the columns of f(h)
+    they need: Fc[:, k] is column cols[k]; every site j needs columns 2j and
+    2j + 1.  Returns (n (2, k), chi (2, 4, k), F (4, k)) for the k sites, the
+    same entries `observables` reads from a full matrix."""
+    pos = {int(c): k for k, c in enumerate(cols)}
+    sites = np.asarray(sites)
+    n = np.empty((2, len(sites)))
+    chi = np.empty((2, 4, len(sites)), dtype=np.complex128)
+    F = np.empty((4, len(sites)), dtype=np.complex128)
+    for k, i in enumerate(sites):
+        c0, c1 = Fc[:, pos[2 * int(i)]], Fc[:, pos[2 * int(i) + 1]]
+        n[0, k] = c0[2 * i].real
+        n[1, k] = 1.0 - c1[2 * i + 1].real
+        for d in range(4):
+            j = model.fwd[d][i]
+            chi[0, d, k] = c0[2 * j]
+            chi[1, d, k] = -np.conj(c1[2 * j + 1])
+        for e in range(4):
+            j = model.nn4[e][i]
+            F[e, k] = -np.conj(c0[2 * j + 1])
+    return n, chi, F

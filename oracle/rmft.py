@@ -294,3 +294,70 @@ def update(params, obs, n_target, mu_eff, alpha=0.5, alpha_n=0.05, eta=0.5, para
     new = (1.0 - alpha) * params + alpha * o
     new[:2 * N] = (1.0 - alpha_n) * params[:2 * N] + alpha_n * o[:2 * N]
     return new, mu_eff - eta * e, r, e
+
+
+# ----------------------------------------------------------------------------- Anderson mixing (reading R4)
+
+class Anderson:
+    """Anderson (Pulay) acceleration of the fixed-point iteration x = G(x).
+
+    The paper does not say how its self-consistency loop is mixed (reading
+    R1 gives linear mixing).  Reading R4 adds the textbook Anderson scheme
+    (Anderson 1965; Walker and Ni 2011), preconditioned by the linear mixing
+    B (alpha_n on the densities, alpha on chi and F, eta on mu_eff):
+
+      f_k   = B (G(x_k) - x_k)
+      dX_j  = x_{j+1} - x_j,  dF_j = f_{j+1} - f_j   over the last m iterations
+      gamma = argmin_g |f_k - dF g|_2   (normal equations, Tikhonov 1e-10 tr/m_k)
+      x_{k+1} = x_k + f_k - (dX + dF) gamma
+
+    With m = 0 (or no history yet) this is the linear mixing step x + f.
+    """
+
+    def __init__(self, m):
+        self.m = int(m)
+        self.dX, self.dF = [], []
+        self.prev = None
+
+    def step(self, x, f):
+        x = np.asarray(x, dtype=np.float64)
+        f = np.asarray(f, dtype=np.float64)
+        if self.m > 0 and self.prev is not None:
+            self.dX.append(x - self.prev[0])
+            self.dF.append(f - self.prev[1])
+            if len(self.dX) > self.m:
+                self.dX.pop(0)
+                self.dF.pop(0)
+        self.prev = (x.copy(), f.copy())
+        if self.m == 0 or not self.dX:
+            return x + f
+        dF = np.array(self.dF).T
+        dX = np.array(self.dX).T
+        G = dF.T @ dF
+        tr = float(np.trace(G))
+        if not (0.0 < tr < 1e300):
+            return x + f
+        G = G + 1e-10 * tr / G.shape[0] * np.eye(G.shape[0])
+        gamma = np.linalg.solve(G, dF.T @ f)
+        return x + f - (dX + dF) @ gamma
+
+
+def update_anderson(params, obs, n_target, mu_eff, mixer, alpha=0.5, alpha_n=0.05, eta=0.5, paramagnetic=True):
+    """`update` with Anderson mixing (reading R4) on x = (params, mu_eff):
+    the processed observables (steps 1-2 of `update`) give G(x); the residual r
+    is the same max |p_new - p| as in `update`.  Returns (params, mu_eff, r, e)."""
+    N = params.size // 26
+    o = np.array(obs, dtype=np.float64, copy=True)
+    if paramagnetic:
+        avg = 0.5 * (o[:N] + o[N:2 * N])
+        o[:N] = avg
+        o[N:2 * N] = avg
+    e = float(np.sum(o[:2 * N]) / N) - n_target
+    o[:2 * N] -= 0.5 * e
+    r = residual(params, o)
+    B = np.full(params.size, alpha)
+    B[:2 * N] = alpha_n
+    x = np.concatenate([params, [mu_eff]])
+    f = np.concatenate([B * (o - params), [-eta * e]])
+    xn = mixer.step(x, f)
+    return xn[:-1], float(xn[-1]), r, e

@@ -139,3 +139,22 @@ def test_observable_extraction_uses_both_column_kinds():
     for e in range(4):
         j = model.nn4[e]
         assert np.max(np.abs(F1[2 * j, 2 * i + 1] + F[(e + 2) % 4][j])) < 1e-13
+
+
+def test_observables_at_sites_equals_full_readout():
+    """The per-site readout from a few columns equals the full-matrix readout."""
+    from oracle import bdg, kpm as okpm, rmft
+    from paper_2212_05685_gb300 import inputs
+    nx, ny, M = 6, 5, 40
+    om = rmft.Model(nx, ny)
+    f = rmft.fields(om, inputs.random_params(nx, ny, 12), 0.2)
+    a, b = bdg.gershgorin(om, f)
+    F1, _ = okpm.f_spectral(bdg.dense(om, f), a, b, M)
+    ref = okpm.observables(om, F1)
+    sites = np.array([0, 7, 29, 13])
+    cols = np.sort(np.concatenate([2 * sites, 2 * sites + 1]))
+    n, chi, F = okpm.observables_at(om, F1[:, cols], cols, sites)
+    rn, rc, rF = rmft.split(ref, om.N)
+    assert np.array_equal(n, rn[:, sites])
+    assert np.array_equal(chi, rc[:, :, sites])
+    assert np.array_equal(F, rF[:, sites])

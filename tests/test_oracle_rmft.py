@@ -131,3 +131,96 @@ def test_update_rule():
     assert np.allclose(new[:N], 0.1 * (avg - 0.5 * e_ref))
     assert np.allclose(new[2 * N:], 0.5 * o[2 * N:])
     assert r == pytest.approx(np.max(np.abs(o[2 * N:])))
+
+
+# ---------------------------------------------------------------- magnetic points (m != 0)
+# Values of App. A's Gutzwiller factors worked out by hand (exact fractions)
+# at two magnetic points, written here as literals with their derivation.
+#
+# Point A: n_up = 1/2, n_dn = 3/10 -> delta = 1/5, m = 1/10, P = 1 - delta^2 + 4 m^2 = 1
+#   g^t_up^2 = 2 delta (1 - delta)/P * (1 + delta + 2m)/(1 + delta - 2m) = (8/25)(7/5) = 56/125
+#   g^t_dn^2 = (8/25)(1/(7/5))                                            = 8/35
+#   g^xy     = 2 (1 - delta)/P                                            = 8/5
+# Point B: n_up = 9/20, n_dn = 2/5 -> delta = 3/20, m = 1/40, P = 1 - 9/400 + 1/400 = 49/50
+#   g^t_up^2 = (2 (3/20)(17/20)/(49/50)) (6/5)/(11/10) = (51/196)(12/11)  = 153/539
+#   g^t_dn^2 = (51/196)(11/12)                                           = 187/784
+#   g^xy     = (17/10)/(49/50)                                           = 85/49
+from fractions import Fraction as Fr  # noqa: E402
+
+
+def _magnetic_params(nx, ny, dens, chi=None, F=None):
+    N = nx * ny
+    n = np.zeros((2, N))
+    n[0], n[1] = 0.45, 0.45
+    for i, (nu, nd) in dens.items():
+        n[0, i], n[1, i] = nu, nd
+    c = np.zeros((2, 4, N), dtype=np.complex128)
+    f = np.zeros((4, N), dtype=np.complex128)
+    for (s, d, i), v in (chi or {}).items():
+        c[s, d, i] = v
+    for (e, i), v in (F or {}).items():
+        f[e, i] = v
+    return inputs.pack(n, c, f)
+
+
+@pytest.mark.parametrize("nu,nd,gt_up2,gt_dn2,gxy", [
+    (Fr(1, 2), Fr(3, 10), Fr(56, 125), Fr(8, 35), Fr(8, 5)),
+    (Fr(9, 20), Fr(2, 5), Fr(153, 539), Fr(187, 784), Fr(85, 49)),
+])
+def test_gutzwiller_site_factors_at_magnetic_points(nu, nd, gt_up2, gt_dn2, gxy):
+    n = np.array([[float(nu)], [float(nd)]])
+    sf = rmft.site_factors(n)
+    assert sf["gt"][0, 0] == pytest.approx(float(gt_up2) ** 0.5, rel=1e-14)
+    assert sf["gt"][1, 0] == pytest.approx(float(gt_dn2) ** 0.5, rel=1e-14)
+    assert sf["gxy"][0] == pytest.approx(float(gxy), rel=1e-14)
+
+
+def test_gsz_and_X_of_a_magnetic_bond():
+    """One x bond i -> j with m_i = 1/10, m_j = -1/10 (point A and its mirror
+    n_up <-> n_dn, both delta = 1/5, P = 1), chi_up = 3/10, chi_dn = 1/10
+    (chibar = 1/5), Delta_up = F_ij = 2/5, Delta_dn = F_ji = 1/5 (Deltabar = 3/10):
+      X = 1 + 12 (4/5)(4/5)/sqrt(1 * 1) = 217/25
+      A = 2 (|Deltabar|^2 - |chibar|^2) = 2 (9/100 - 4/100) = 1/10
+      c = 4 m_i m_j = -1/25
+      R = (A - c X^2)/(A - c) = (1/10 + 47089/15625)/(7/50) = 97303/4375
+      g^xy_ij = (8/5)(8/5) = 64/25,  g^z_ij = (64/25)(97303/4375)
+    and the bond's exchange energy (reading W2)
+      J [g^z (m_i m_j - (|chi_up|^2 + |chi_dn|^2 + |D_up|^2 + |D_dn|^2)/4)
+         - g^xy Re(chi_up chi_dn* + D_up* D_dn)]
+      = J [g^z (-1/100 - 3/40) - (64/25)(3/100 + 2/25)]."""
+    nx, ny = 4, 2
+    om = rmft.Model(nx, ny, flux=0)
+    i, j = 0, 1
+    p = _magnetic_params(nx, ny, {i: (0.5, 0.3), j: (0.3, 0.5)},
+                         chi={(0, 0, i): 0.3, (1, 0, i): 0.1},
+                         F={(0, i): 0.4, (2, j): 0.2})
+    n, chi, F = rmft.split(p, om.N)
+    sf = rmft.site_factors(n)
+    b = rmft._bond_exchange(om, sf, n, chi, F, 0)
+    X = Fr(217, 25)
+    R = Fr(97303, 4375)
+    gz = Fr(64, 25) * R
+    assert b["X"][i] == pytest.approx(float(X), rel=1e-14)
+    assert b["R"][i] == pytest.approx(float(R), rel=1e-13)
+    assert b["gz"][i] == pytest.approx(float(gz), rel=1e-13)
+    Ebond = om.J * (float(gz) * (-0.01 - 0.075) - 2.56 * (0.03 + 0.08))
+    assert b["W"][i] == pytest.approx(Ebond, rel=1e-13)
+
+
+def test_W_of_a_magnetic_bond_configuration():
+    """W of the configuration above (zero field, only the bond i -> j carries
+    chi and F, every other site paramagnetic so no other bond has m_i m_j != 0):
+      hopping  -2 t (g^t_i,up g^t_j,up chi_up + g^t_i,dn g^t_j,dn chi_dn)
+               with g^t_j,up = g^t_i,dn and g^t_j,dn = g^t_i,up (mirror point),
+               g^t_i,up g^t_j,up = sqrt((56/125)(8/35)) = sqrt(64/625) = 8/25:
+               -2 (8/25)(3/10 + 1/10) = -32/125
+      exchange the bond energy of the previous test
+      mu term  0 (mu = 0)."""
+    nx, ny = 4, 2
+    om = rmft.Model(nx, ny, flux=0)
+    p = _magnetic_params(nx, ny, {0: (0.5, 0.3), 1: (0.3, 0.5)},
+                         chi={(0, 0, 0): 0.3, (1, 0, 0): 0.1}, F={(0, 0): 0.4, (2, 1): 0.2})
+    gz = float(Fr(64, 25) * Fr(97303, 4375))
+    hop = -32.0 / 125.0
+    exch = om.J * (gz * (-0.01 - 0.075) - 2.56 * (0.03 + 0.08))
+    assert rmft.energy_W(om, p, 0.0) == pytest.approx(hop + exch, rel=1e-13)
