@@ -95,6 +95,15 @@ typedef struct {
                            F_M(h~) is estimated as conj(xi_J) F_M(h~) r_colour(J).
                            kpm_observables and rmft_iterate only. */
   int32_t probe_seed;   /* phase stream of the probing vectors */
+  int32_t site_begin;   /* column range of the pass (App. B: every start vector is an     */
+  int32_t site_end;     /* independent recursion): 0, 0 = all sites; else only the unit
+                           columns (j, up), (j, dn) of sites j in [site_begin, site_end),
+                           0 <= site_begin < site_end <= N, are propagated; obs holds the
+                           order parameters of those sites and 0 elsewhere, omega the part
+                           of the trace over those columns, so the obs of a partition of the
+                           sites sum to the full pass exactly and the omegas to rounding.
+                           kpm_observables and kpm_backward (its gradient is then the part
+                           from those columns); with probing, KPM_EINVAL. */
   int32_t reserved;     /* 0 */
 } kpm_opts;
 
@@ -121,7 +130,17 @@ typedef struct {
   double eta;           /* gain of the chemical-potential feedback (0.5) */
   double tol;           /* converged when max |p_new - p| and |<n> - n_target| < tol */
   int32_t paramagnetic; /* 1: keep n_up = n_dn (m = 0 sector) */
-  int32_t reserved;
+  int32_t strict;       /* 1: rmft_iterate returns KPM_ENOTCONV when its n_iter iterations
+                           end without meeting tol (stats and params as after the last
+                           iteration); 0: KPM_OK, with stats.converged = 0 */
+  int32_t anderson;     /* 0: linear mixing (above).  1..16: Anderson (Pulay) mixing over the
+                           last `anderson` iterations of this call (history cleared at the
+                           start of every call), applied to the parameters and mu_eff with
+                           the linear mixings as preconditioner (reading R4) */
+  int32_t sync_every;   /* iterations per host read of the residual (0 or 1: every
+                           iteration).  k > 1: k iterations are queued between reads; an
+                           iteration that meets tol freezes params and mu_eff on the device,
+                           so results, stats and iteration counts equal those of k = 1 */
 } kpm_rmft_opts;
 
 /* Per-call results of rmft_iterate (host struct, filled before return). */
@@ -133,7 +152,8 @@ typedef struct {
   double a, b;          /* spectral rescale h~ = (h - b)/a of the last pass */
   double recursion_ms;  /* device time of the Chebyshev recursion steps, summed over
                            this call's iterations (CUDA events recorded on the
-                           launching stream around the step launches) */
+                           launching stream around the step launches; with sync_every
+                           k > 1 the last iteration of each group of k counts k times) */
   double recursion_bytes; /* algorithmic HBM bytes of those launches, summed the same
                            way: slab vectors each launch must read and write
                            (8 B per FP32 / 16 B per FP64 complex element) */
@@ -151,13 +171,32 @@ int kpm_destroy(kpm_ctx* ctx);
 int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes);
 /* Synchronise `stream` (NULL: the legacy default stream) and read the device
  * fault word of the FP32 recursion: KPM_OK; KPM_ETIMEDOUT when one of its
- * bounded waits for its own TMA copies expired (that launch and every later
- * FP32 recursion launch of the process wrote NaN instead of results; the word
- * is never cleared); KPM_ECUDA for an asynchronous CUDA error or a recursion
- * that found its shared memory misaligned for TMA (outputs NaN as well).
- * rmft_iterate and rmft_iterate_batched read the word themselves when an
- * iteration turns non-finite. */
+ * bounded waits for its own TMA copies expired (that launch, and every FP32
+ * recursion launch of the process after it until the word is cleared, wrote
+ * NaN instead of results); KPM_ECUDA for an asynchronous CUDA error or a
+ * recursion that found its shared memory misaligned for TMA (outputs NaN as
+ * well).  A word that is reported is cleared (after the device is idle), so
+ * later launches compute again; the caller decides whether to trust the
+ * device further.  rmft_iterate and rmft_iterate_batched read (and clear) the
+ * word themselves when an iteration turns non-finite. */
 int kpm_sync_status(kpm_ctx* ctx, void* stream);
+/* Failure-path test hook (no counterpart in the paper).  The next `count` CTAs
+ * of the TMA-staged FP32 recursion step that would issue the copy of their
+ * third window row skip that copy and its expected byte count, so nothing is
+ * in flight for that slot and the CTA's bounded waits expire: the launch
+ * writes NaN and the fault word reads KPM_ETIMEDOUT, with no device fault.
+ * wait_limit_s > 0 sets the bounded-wait limit of every later FP32 recursion
+ * launch in the process (default 2 s); <= 0 restores the default.  count = 0
+ * withdraws outstanding skips.  Synchronises the device. */
+int kpm_inject_lost_copy(kpm_ctx* ctx, int count, double wait_limit_s);
+/* Measured ALU peaks of the device (no counterpart in the paper; the
+ * denominators of the FP64 and double-float rooflines): independent FMA
+ * chains, 8 per thread, 4 CTAs of 256 threads per SM, timed with CUDA events on
+ * `stream`.  out[0] = FP64 FMA TFLOP/s (2 flops per FMA), out[1] = FP32 scalar
+ * FMA TFLOP/s, out[2] = FP32 packed f32x2 FMA TFLOP/s (4 flops per
+ * instruction), out[3] = median SM clock seen by the kernels in MHz (from
+ * %clock64 over %globaltimer).  out: host, 4 doubles.  Synchronises `stream`. */
+int kpm_measure_peaks(kpm_ctx* ctx, double* out, void* stream);
 const char* kpm_strerror(int status);
 /* Last error message of this context (static storage of the context). */
 const char* kpm_last_error(const kpm_ctx* ctx);
@@ -211,6 +250,25 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts,
                  const kpm_rmft_opts* ropts, const double* phi, double* params,
                  double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);
 
+/* The two halves of one rmft_iterate iteration, for drivers that shard the
+ * KPM pass over GPUs by sites (kpm_opts.site_begin/site_end) and merge the
+ * observables themselves (App. A self-consistency; App. B: the start vectors
+ * are independent).  rmft_prepare: fields from params at mu_eff with the mean
+ * site energy taken out (reading R2), then the Gershgorin bounds (b = 0 exactly
+ * with KPM_FLAG_PH_HALF in opts).  fields: 26 N, ab: 2 doubles, mu_out: 1
+ * double (the Lagrange multiplier mu = mu_eff + <dW/dn|_{mu=0}>), all device;
+ * phi, params, mu_eff device.  rmft_update: the mixing update of
+ * rmft_iterate from the observables of the whole lattice (linear mixing;
+ * anderson must be 0): params and mu_eff updated in place, obs overwritten by
+ * the processed observables, stats_out (device, 2 doubles) = {max |p_new - p|,
+ * <n_new> - n_target}.  Every rank that runs rmft_update on the same merged
+ * obs computes bit-identical params. */
+int rmft_prepare(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* phi,
+                 const double* params, const double* mu_eff, double* fields, double* ab, double* mu_out,
+                 void* stream);
+int rmft_update(kpm_ctx* ctx, const kpm_model* model, const kpm_rmft_opts* ropts, double* params, double* obs,
+                double* mu_eff, double* stats_out, void* stream);
+
 /* Autotuner of the recursion launch: times a short pass (M = 32) for every
  * slab width in {D, 8192, ..., 128} (narrow slabs keep both recursion
  * vectors in L2), every column chunk that fits shared memory and (FP32) one
@@ -263,16 +321,23 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
  *
  * No context and no allocation: every intermediate lives in a file-scope
  * device array of 48 MiB (per GPU, held by every GPU that loads the library
- * until the process exits).  The first call on a device resolves that array's
- * address with the device current; make it before any stream capture.  All
- * calls on a device share the array: calls whose GPU work overlaps (other
- * streams, other host threads) race, so serialise them.  Each call rewrites
- * every scratch byte it reads.  The recursion slab is narrowed to what fits
- * (block_width is an upper bound); a lattice or M whose fixed intermediates
- * (4M doubles, 26N stencil entries, 10 accumulators per column, one column
- * chunk of both slabs) exceed 48 MiB returns KPM_EINVAL.  Arguments as for
- * kpm_observables, with the current device; result within rounding of
- * kpm_observables (identical arithmetic, possibly a different slab width). */
+ * until the process exits).  Calls outside stream capture resolve that
+ * array's address with the device current (so a device reset that reloads the
+ * module is followed); a call on a capturing stream reuses the address of the
+ * last call outside capture on that device, so make one call before
+ * capturing.  All calls on a device share the array: calls whose GPU work
+ * overlaps (other streams, other host threads) race, so serialise them.  Each
+ * call rewrites every scratch byte it reads.  The recursion slab is narrowed
+ * to what fits (block_width is an upper bound); a lattice or M whose fixed
+ * intermediates (4M doubles, 26N stencil entries, 10 accumulators per column,
+ * one column chunk of both slabs) exceed 48 MiB returns KPM_EINVAL.
+ * Arguments as for kpm_observables (all sites: site_begin = site_end = 0;
+ * negative block_width or cols_per_block: KPM_EINVAL), device pointers of the
+ * current device; result within rounding of kpm_observables (identical
+ * arithmetic, possibly a different slab width).  The FP32 recursion's bounded
+ * waits behave as in kpm_observables: a device failure shows as NaN in obs,
+ * and kpm_sync_status (with any context of the device) reports and clears the
+ * fault word. */
 int kpm_observables_noalloc(const kpm_model* model, const kpm_opts* opts, const double* fields,
                             const double* ab, double* obs, double* omega, void* stream);
 

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libkpm.so")
-SOURCES = ["cheb_kernels.cu", "rmft_kernels.cu", "kpm_api.cu", "kpm_noalloc.cu", "kpm_adjoint.cu", "kpm_ldos.cu"]
+SOURCES = ["cheb_kernels.cu", "rmft_kernels.cu", "kpm_api.cu", "kpm_noalloc.cu", "kpm_adjoint.cu", "kpm_ldos.cu", "kpm_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -722,6 +722,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: orders of magnitude above a lattice row's copies
+// bounded-wait limit of the TMA step (kWaitLimitNs unless a test shortened it)
+// and the number of CTAs that are still to skip one window copy (test hook of
+// the failure path: a skipped copy leaves nothing in flight, so only the
+// waits on its slot run out)
+__device__ unsigned long long g_wait_limit_ns = kWaitLimitNs;
+__device__ int g_drop_copy;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
@@ -801,10 +807,15 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   // window row w holds lattice row y0 - 1 + w (w = 0 .. nrow + 1) in slot w % 5,
   // coefficient row c holds row y0 + c (c = 0 .. nrow - 1) in slot c % 3
   int w_hi = -1, c_hi = -1;  // last window / coefficient row issued (issuing thread)
+  const uint64_t wlim = *reinterpret_cast<volatile unsigned long long*>(&g_wait_limit_ns);
   auto issue_v = [&](int w) {
     const int ly = wrapi(y0 - 1 + w, ny);
     const uint32_t bar = bar0 + 8 * (w % 5);
     const uint32_t dst = smem_u32(win + (w % 5) * rowsz);
+    if (w == 2 && *reinterpret_cast<volatile int*>(&g_drop_copy) > 0 && atomicSub(&g_drop_copy, 1) > 0) {
+      w_hi = w;  // skipped: the slot's phase never completes
+      return;
+    }
     mbar_expect_tx(bar, vbytes);
     for (int b = 0; b < nbox; ++b)
       tma_load_2d(dst + (uint32_t)(b * brows * CB * 8), tm, (int)(2 * cb0), 2 * nx * ly + b * brows, bar);
@@ -877,12 +888,12 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     const int rot_next = next_rot(rot);
     if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, rot_next, nxt);
     bool ok = true;
-    if (q == 0) ok = mbar_wait(vbar(0), 0, kWaitLimitNs) && mbar_wait(vbar(1), 0, kWaitLimitNs);
-    ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), kWaitLimitNs) && mbar_wait(cbar(q), cpar(q), kWaitLimitNs);
+    if (q == 0) ok = mbar_wait(vbar(0), 0, wlim) && mbar_wait(vbar(1), 0, wlim);
+    ok = ok && mbar_wait(vbar(q + 2), vpar(q + 2), wlim) && mbar_wait(cbar(q), cpar(q), wlim);
     if (threadIdx.x == 0 && ok) {
       // window row y+3 into the slot of y-2 and coefficients of y+2 into the
       // slot of y-1, once every warp has finished row y-1 (row 0: fresh slots)
-      if (q >= 1) ok = mbar_wait(dbar(q - 1), dpar(q - 1), kWaitLimitNs);
+      if (q >= 1) ok = mbar_wait(dbar(q - 1), dpar(q - 1), wlim);
       if (ok) {
         if (q + 4 <= nrow + 1) issue_v(q + 4);
         if (q + 2 < nrow) issue_c(q + 2);
@@ -937,8 +948,8 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     // the last fill of every slot before the shared memory is released
     if (threadIdx.x == 0) {
       atomicOr(&g_step_fault, 1u);
-      for (int w = max(0, w_hi - 4); w <= w_hi; ++w) mbar_wait(vbar(w), vpar(w), kWaitLimitNs / 4);
-      for (int c = max(0, c_hi - 2); c <= c_hi; ++c) mbar_wait(cbar(c), cpar(c), kWaitLimitNs / 4);
+      for (int w = max(0, w_hi - 4); w <= w_hi; ++w) mbar_wait(vbar(w), vpar(w), wlim / 4);
+      for (int c = max(0, c_hi - 2); c <= c_hi; ++c) mbar_wait(cbar(c), cpar(c), wlim / 4);
     }
     __syncthreads();
     poison();
@@ -1690,6 +1701,18 @@ cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPt
 
 cudaError_t read_step_fault(unsigned int* out) {
   return cudaMemcpyFromSymbol(out, g_step_fault, sizeof(unsigned int));
+}
+
+cudaError_t clear_step_fault() {
+  const unsigned int zero = 0u;
+  return cudaMemcpyToSymbol(g_step_fault, &zero, sizeof(zero));
+}
+
+cudaError_t set_step_failure_test(int drop_copies, uint64_t wait_limit_ns) {
+  cudaError_t e = cudaMemcpyToSymbol(g_drop_copy, &drop_copies, sizeof(int));
+  if (e != cudaSuccess) return e;
+  const unsigned long long lim = wait_limit_ns ? wait_limit_ns : kWaitLimitNs;
+  return cudaMemcpyToSymbol(g_wait_limit_ns, &lim, sizeof(lim));
 }
 
 cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s) {

@@ -48,7 +48,7 @@ __device__ __forceinline__ void slab_add(void* V, int prec, int64_t ldv, int64_t
 // Seed weights of every unit column from the upstream gradients (readings
 // N2, N3 transposed): w[J][s] with dL = Re sum conj(W_KJ) dF_KJ.
 __global__ void seed_weights_kernel(int nx, int ny, const double* __restrict__ g, const double* __restrict__ ab,
-                                    double g_omega, double2* __restrict__ w) {
+                                    double g_omega, double2* __restrict__ w, int sb, int se) {
   const int N = nx * ny;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
@@ -57,6 +57,10 @@ __global__ void seed_weights_kernel(int nx, int ny, const double* __restrict__ g
   const double* gF = g + 18 * N;
   double2* w0 = w + (size_t)(2 * j) * kSlots;
   double2* w1 = w + (size_t)(2 * j + 1) * kSlots;
+  if (j < sb || j >= se) {  // columns outside the pass's site range
+    for (int k = 0; k < kSlots; ++k) w0[k] = w1[k] = make_double2(0.0, 0.0);
+    return;
+  }
   w0[0] = make_double2(gn[j], 0.0);
   w1[0] = make_double2(-gn[N + j], 0.0);
   for (int d = 0; d < 4; ++d) {
@@ -391,9 +395,9 @@ __global__ void grad_fields_kernel(int nx, int ny, const double2* __restrict__ G
 }  // namespace
 
 cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const double* ab, double g_omega,
-                                double2* w, cudaStream_t s) {
+                                double2* w, cudaStream_t s, int sb, int se) {
   const int N = nx * ny;
-  seed_weights_kernel<<<(N + 127) / 128, 128, 0, s>>>(nx, ny, grad_obs, ab, g_omega, w);
+  seed_weights_kernel<<<(N + 127) / 128, 128, 0, s>>>(nx, ny, grad_obs, ab, g_omega, w, sb, se < 0 ? N : se);
   return cudaGetLastError();
 }
 

@@ -49,7 +49,12 @@ struct kpm_ctx {
   double* dparams = nullptr;    // 26 N (host-pointer staging)
   double* dphi = nullptr;       // 4 N
   size_t site_n = 0;
-  double* misc = nullptr;       // [0..1] ab, [2] mu, [3] omega, [4..5] stats, [6] mean, [7] mu_eff, [8] W
+  double* misc = nullptr;       // [0..1] ab, [2] mu, [3] omega, [4..5] stats, [6] mean, [7] mu_eff, [8] W,
+                                // [16..31] record of the iteration loop (launch_update)
+  double* and_buf = nullptr;    // Anderson mixing state
+  size_t and_bytes = 0;
+  double* peak_buf = nullptr;   // scratch of kpm_measure_peaks
+  size_t peak_bytes = 0;
   // adjoint scratch: checkpoints, segment, lambda buffers; stencil gradient; seed weights
   void* bwd = nullptr;
   size_t bwd_bytes = 0;
@@ -188,6 +193,9 @@ struct PassPlan {
   int64_t width;  // unit columns per slab
   size_t elem;    // bytes per complex
   bool dbl;       // FP32 double-step recursion (four slabs)
+  int64_t c0, c1; // pass columns [c0, c1) (all: 0, pass_columns)
+  int sb, se;     // sites whose observables the pass writes (all: 0, N)
+  bool ranged;    // a proper sub-range of the sites
 };
 
 // the widest equal split of D unit columns into slabs of at most `width`
@@ -212,10 +220,26 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
     return fail(ctx, KPM_EINVAL, "probe_p must be 0 or >= 2 and divide nx and ny");
   if (pp_ > 0 && (o->flags & KPM_FLAG_PH_HALF))
     return fail(ctx, KPM_EINVAL, "probing and KPM_FLAG_PH_HALF do not combine");
+  const int N = m->nx * m->ny;
+  pp->sb = 0;
+  pp->se = N;
+  pp->ranged = false;
+  if (o->site_begin != 0 || o->site_end != 0) {
+    if (!(o->site_begin >= 0 && o->site_begin < o->site_end && o->site_end <= N))
+      return fail(ctx, KPM_EINVAL, "site range must satisfy 0 <= site_begin < site_end <= N");
+    pp->sb = o->site_begin;
+    pp->se = o->site_end;
+    pp->ranged = !(pp->sb == 0 && pp->se == N);
+    if (pp->ranged && pp_ > 0) return fail(ctx, KPM_EINVAL, "probing and a site range do not combine");
+    if (pp->ranged && (o->flags & KPM_FLAG_PH_HALF))
+      return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF and a site range do not combine");
+  }
   const bool want_dbl = o->precision == KPM_FP32 && (o->flags & KPM_FLAG_DOUBLE_STEP) && pp_ == 0;
   const int js = (o->flags & KPM_FLAG_PH_HALF) ? 1 : 0;
-  // start vectors of the pass: unit columns, or R = 2 p^2 probing vectors
-  const int64_t ncols = pp_ > 0 ? std::min<int64_t>(D, 2 * (int64_t)pp_ * pp_) : (D >> js);
+  // start vectors of the pass: unit columns (those of the site range), or R = 2 p^2 probing vectors
+  pp->c0 = pp->ranged ? 2 * (int64_t)pp->sb : 0;
+  pp->c1 = pp->ranged ? 2 * (int64_t)pp->se : (pp_ > 0 ? std::min<int64_t>(D, 2 * (int64_t)pp_ * pp_) : (D >> js));
+  const int64_t ncols = pp->c1 - pp->c0;
   int64_t width = o->block_width > 0 ? std::min<int64_t>(o->block_width, ncols) : ncols;
   if (o->block_width == 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((want_dbl ? 4 : 2) * (uint64_t)D * pp->elem));
@@ -309,7 +333,6 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   int nl = 0, nr = 0;
   double nb = 0.0;
   const double vec = (double)p.D * (double)p.ldv * (double)pp.elem;  // bytes of one slab vector
-  const int64_t ncols = pass_columns(p);
   KPM_CU(launch_coefficients(M, ab, ctx->am, ctx->ao, s, p.js, o->temperature));
   if (prec == KPM_FP32)
     KPM_CU(launch_scale_table_f32(*m, fields, ab, (float2*)ctx->table, s));
@@ -318,7 +341,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   else
     KPM_CU(launch_scale_table_f64(*m, fields, ab, (double2*)ctx->table, s));
   nl += 2;
-  for (int64_t s0 = 0; s0 < ncols; s0 += pp.width) {
+  for (int64_t s0 = pp.c0; s0 < pp.c1; s0 += pp.width) {
     // X0 = V_{mm-1}, X1 = V_mm; Y0, Y1 the free pair of the double-step recursion
     void* X0 = ctx->slab[0];
     void* X1 = ctx->slab[1];
@@ -326,7 +349,7 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
     void* Y1 = pp.dbl ? ctx->slab[3] : nullptr;
     KPM_CU(launch_cheb_init(p, prec, X0, s0, ctx->acc, ctx->am, ctx->ao, s));
     nl += 1;
-    if (events && s0 == 0) KPM_CU(cudaEventRecordWithFlags(ctx->ev[0], s, cudaEventRecordExternal));
+    if (events && s0 == pp.c0) KPM_CU(cudaEventRecordWithFlags(ctx->ev[0], s, cudaEventRecordExternal));
     if (M >= 2) {
       KPM_CU(launch_cheb_step(p, prec, ctx->table, X0, X1, s0, ctx->acc, ctx->am, ctx->ao, 0, 0, s));
       nr += 1;
@@ -349,13 +372,13 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
       nb += 3 * vec;
       std::swap(X0, X1);
     }
-    if (events && s0 + pp.width >= ncols) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
+    if (events && s0 + pp.width >= pp.c1) KPM_CU(cudaEventRecordWithFlags(ctx->ev[1], s, cudaEventRecordExternal));
     if (M >= 2) {
       KPM_CU(launch_cheb_gather(p, prec, X1, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
       nl += 1;
     }
   }
-  KPM_CU(launch_assemble(m->nx, m->ny, ctx->acc, ab, obs, omega, ctx->red, s, p.js));
+  KPM_CU(launch_assemble(m->nx, m->ny, ctx->acc, ab, obs, omega, ctx->red, s, p.js, pp.sb, pp.se));
   nl += omega ? 2 : 1;
   if (launches) *launches = nl0 + nl + nr;
   if (rec_launches) *rec_launches = nr;
@@ -363,17 +386,20 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
   return KPM_OK;
 }
 
+constexpr int kMisc = 32;  // doubles of ctx->misc / host_misc
+constexpr int kRec = 16;   // offset of the iteration record in misc
+
 int ensure_misc(kpm_ctx* ctx) {
   if (ctx->misc) return KPM_OK;
-  if (cudaMalloc(&ctx->misc, 16 * sizeof(double)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->misc, kMisc * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
   }
-  if (cudaMallocHost(&ctx->host_misc, 16 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->host_misc, kMisc * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, KPM_ENOMEM, "cudaMallocHost failed");
   }
-  cudaMemset(ctx->misc, 0, 16 * sizeof(double));
+  cudaMemset(ctx->misc, 0, kMisc * sizeof(double));
   return KPM_OK;
 }
 
@@ -459,6 +485,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   drop_graph(ctx);
   cublas_destroy(ctx->cublas);
   for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->xi, (void*)ctx->ldos_buf,
+                  (void*)ctx->and_buf, (void*)ctx->peak_buf,
                   (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
@@ -480,18 +507,21 @@ int kpm_destroy(kpm_ctx* ctx) {
   return KPM_OK;
 }
 
-// KPM_ETIMEDOUT / KPM_ECUDA for a fault recorded by the FP32 recursion, else 0
+// KPM_ETIMEDOUT / KPM_ECUDA for a fault recorded by the FP32 recursion, else
+// 0; a recorded fault is cleared once the device is idle (the launches that
+// saw it have written NaN by then)
 static int device_fault_status(kpm_ctx* ctx) {
   unsigned int f = 0;
-  const cudaError_t e = read_step_fault(&f);
+  cudaError_t e = read_step_fault(&f);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device fault word");
+  if (f == 0u) return KPM_OK;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceSynchronize");
+  if ((e = clear_step_fault()) != cudaSuccess) return cuda_fail(ctx, e, "clearing the device fault word");
   if (f & 1u)
     return fail(ctx, KPM_ETIMEDOUT,
-                "a bounded wait of the FP32 recursion expired: its outputs and those of every later FP32 recursion "
-                "launch in this process are NaN");
-  if (f & 2u)
-    return fail(ctx, KPM_ECUDA, "shared memory of the FP32 recursion was not aligned for TMA: outputs are NaN");
-  return KPM_OK;
+                "a bounded wait of the FP32 recursion expired: the outputs of that launch, and of every FP32 "
+                "recursion launch after it until this report, are NaN");
+  return fail(ctx, KPM_ECUDA, "shared memory of the FP32 recursion was not aligned for TMA: outputs are NaN");
 }
 
 int kpm_sync_status(kpm_ctx* ctx, void* stream) {
@@ -499,6 +529,27 @@ int kpm_sync_status(kpm_ctx* ctx, void* stream) {
   DeviceGuard g(ctx->device);
   KPM_CU(cudaStreamSynchronize((cudaStream_t)stream));
   return device_fault_status(ctx);
+}
+
+int kpm_inject_lost_copy(kpm_ctx* ctx, int count, double wait_limit_s) {
+  if (!ctx) return KPM_EINVAL;
+  if (count < 0 || !(wait_limit_s < 3600.0)) return fail(ctx, KPM_EINVAL, "count must be >= 0, wait limit < 1 h");
+  DeviceGuard g(ctx->device);
+  KPM_CU(cudaDeviceSynchronize());
+  const uint64_t ns = wait_limit_s > 0.0 ? (uint64_t)(wait_limit_s * 1e9) : 0;
+  KPM_CU(set_step_failure_test(count, ns < 1000 && wait_limit_s > 0.0 ? 1000 : ns));
+  return KPM_OK;
+}
+
+int kpm_measure_peaks(kpm_ctx* ctx, double* out, void* stream) {
+  if (!ctx || !out) return KPM_EINVAL;
+  DeviceGuard g(ctx->device);
+  int sms = 0;
+  KPM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  int r;
+  if ((r = ensure(ctx, &ctx->peak_buf, &ctx->peak_bytes, peak_scratch_bytes(sms)))) return r;
+  KPM_CU(measure_alu_peaks(sms, ctx->peak_buf, out, (cudaStream_t)stream));
+  return KPM_OK;
 }
 
 int kpm_set_scratch_budget(kpm_ctx* ctx, uint64_t bytes) {
@@ -573,6 +624,59 @@ int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, 
   return enqueue_pass(ctx, model, opts, pp, fields, ab, obs, omega, (cudaStream_t)stream);
 }
 
+int check_rmft_opts(kpm_ctx* ctx, const kpm_rmft_opts* ro) {
+  if (!ro) return fail(ctx, KPM_EINVAL, "rmft opts is null");
+  if (!(ro->alpha > 0.0 && ro->alpha <= 1.0 && ro->alpha_n > 0.0 && ro->alpha_n <= 1.0))
+    return fail(ctx, KPM_EINVAL, "mixing must lie in (0, 1]");
+  if (ro->anderson < 0 || ro->anderson > 16) return fail(ctx, KPM_EINVAL, "anderson must lie in 0..16");
+  if (ro->sync_every < 0) return fail(ctx, KPM_EINVAL, "sync_every must be >= 0");
+  return KPM_OK;
+}
+
+int rmft_prepare(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* phi,
+                 const double* params, const double* mu_eff, double* fields, double* ab, double* mu_out,
+                 void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model))) return r;
+  if (!opts) return fail(ctx, KPM_EINVAL, "opts is null");
+  if ((r = check_dev(ctx, phi, "phi")) || (r = check_dev(ctx, params, "params")) ||
+      (r = check_dev(ctx, mu_eff, "mu_eff")) || (r = check_dev(ctx, fields, "fields")) ||
+      (r = check_dev(ctx, ab, "ab")) || (r = check_dev(ctx, mu_out, "mu_out")))
+    return r;
+  if (!(opts->margin >= 0.0)) return fail(ctx, KPM_EINVAL, "margin must be >= 0");
+  DeviceGuard g(ctx->device);
+  const int N = model->nx * model->ny;
+  if ((r = ensure_misc(ctx))) return r;
+  if (!ctx->red && cudaMalloc(&ctx->red, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  KPM_CU(launch_fields(*model, phi, params, 0.0, fields, nullptr, s));
+  KPM_CU(launch_shift_eps(N, fields, mu_eff, ctx->misc + 6, mu_out, ctx->red, s));
+  KPM_CU(launch_gershgorin(*model, fields, opts->margin, ab, ctx->red, s, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0));
+  return KPM_OK;
+}
+
+int rmft_update(kpm_ctx* ctx, const kpm_model* model, const kpm_rmft_opts* ropts, double* params, double* obs,
+                double* mu_eff, double* stats_out, void* stream) {
+  if (!ctx) return KPM_EINVAL;
+  int r;
+  if ((r = check_model(ctx, model)) || (r = check_rmft_opts(ctx, ropts))) return r;
+  if (ropts->anderson != 0) return fail(ctx, KPM_EINVAL, "rmft_update mixes linearly (anderson must be 0)");
+  if ((r = check_dev(ctx, params, "params")) || (r = check_dev(ctx, obs, "obs")) ||
+      (r = check_dev(ctx, mu_eff, "mu_eff")) || (r = check_dev(ctx, stats_out, "stats_out")))
+    return r;
+  DeviceGuard g(ctx->device);
+  if (!ctx->red && cudaMalloc(&ctx->red, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KPM_ENOMEM, "cudaMalloc failed");
+  }
+  KPM_CU(launch_update(model->nx * model->ny, params, obs, mu_eff, *ropts, stats_out, ctx->red, (cudaStream_t)stream));
+  return KPM_OK;
+}
+
 int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const kpm_rmft_opts* ropts,
                  const double* phi, double* params, double* mu_eff, int n_iter, kpm_rmft_stats* stats,
                  void* stream) {
@@ -581,16 +685,23 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   if ((r = check_model(ctx, model))) return r;
   if (!ropts || !phi || !params || !mu_eff) return fail(ctx, KPM_EINVAL, "null argument");
   if (n_iter < 0) return fail(ctx, KPM_EINVAL, "n_iter must be >= 0");
-  if (!(ropts->alpha > 0.0 && ropts->alpha <= 1.0 && ropts->alpha_n > 0.0 && ropts->alpha_n <= 1.0))
-    return fail(ctx, KPM_EINVAL, "mixing must lie in (0, 1]");
+  if ((r = check_rmft_opts(ctx, ropts))) return r;
   DeviceGuard g(ctx->device);
   const int N = model->nx * model->ny;
   cudaStream_t s = (cudaStream_t)stream;
   PassPlan pp;
   if ((r = plan_pass(ctx, model, opts, &pp))) return r;
+  if (pp.ranged) return fail(ctx, KPM_EINVAL, "rmft_iterate needs the whole lattice (site range 0, 0)");
   if ((r = ensure_site_scratch(ctx, N))) return r;
   if ((r = ensure_pass_scratch(ctx, model, opts, pp))) return r;
   if ((r = ensure_misc(ctx))) return r;
+  AndersonState an;
+  if (ropts->anderson > 0) {
+    const size_t need = anderson_doubles(N, ropts->anderson) * sizeof(double);
+    if (ctx->and_bytes < need) drop_graph(ctx);
+    if ((r = ensure(ctx, &ctx->and_buf, &ctx->and_bytes, need))) return r;
+    an = anderson_state(N, ropts->anderson, ctx->and_buf);
+  }
 
   // host or device buffers: stage host ones through the context
   const bool params_dev = is_device_ptr(params);
@@ -632,14 +743,15 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     if (e == cudaSuccess)
       rr = enqueue_pass(ctx, model, opts, pp, ctx->fields, ab, ctx->obs, ctx->misc + 3, c, true, &npass, &nrec,
                         &nbytes);
-    // fields 1, mean-shift 3, bounds 2, pass, update 4
-    ctx->launches = 1 + 3 + 2 + npass + 4;
+    // fields 1, mean-shift 3, bounds 2, pass, update 4 (Anderson: 7)
+    ctx->launches = 1 + 3 + 2 + npass + (ropts->anderson > 0 ? 7 : 4);
     ctx->rec_launches = nrec;
     ctx->rec_bytes = nbytes;
     if (e == cudaSuccess && rr == KPM_OK)
-      e = launch_update(N, dpar, ctx->obs, dmu, *ropts, ctx->misc + 4, ctx->red, c);
+      e = launch_update(N, dpar, ctx->obs, dmu, *ropts, ctx->misc + 4, ctx->red, c, ctx->misc + kRec, ctx->misc,
+                        ropts->anderson > 0 ? &an : nullptr);
     if (e == cudaSuccess && rr == KPM_OK)
-      e = cudaMemcpyAsync(ctx->host_misc, ctx->misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c);
+      e = cudaMemcpyAsync(ctx->host_misc + kRec, ctx->misc + kRec, 16 * sizeof(double), cudaMemcpyDeviceToHost, c);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c, &graph);
     if (e != cudaSuccess) {
@@ -666,23 +778,31 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   int status = KPM_OK;
   st.kernel_launches = ctx->launches;
   st.recursion_launches = ctx->rec_launches;
-  for (int it = 0; it < n_iter; ++it) {
-    KPM_CU(cudaGraphLaunch(ctx->graph, s));
+  // a fresh record (iteration count, frozen flag, Anderson history length)
+  // and, for Anderson mixing, an empty history
+  KPM_CU(cudaMemsetAsync(ctx->misc + kRec, 0, 16 * sizeof(double), s));
+  if (ropts->anderson > 0)
+    KPM_CU(cudaMemsetAsync(an.dX, 0, 2 * (size_t)ropts->anderson * (26 * (size_t)N + 1) * sizeof(double), s));
+  const int group = std::max(1, ropts->sync_every);
+  for (int done = 0; done < n_iter;) {
+    const int k = std::min(group, n_iter - done);
+    for (int j = 0; j < k; ++j) KPM_CU(cudaGraphLaunch(ctx->graph, s));
     KPM_CU(cudaStreamSynchronize(s));
+    done += k;
     if (ctx->rec_launches > 0) {
       float ms = 0.f;
       KPM_CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-      st.recursion_ms += ms;
-      st.recursion_bytes += ctx->rec_bytes;
+      st.recursion_ms += (double)ms * k;
+      st.recursion_bytes += ctx->rec_bytes * k;
     }
-    const double* h = ctx->host_misc;
+    const double* h = ctx->host_misc + kRec;
     st.a = h[0];
     st.b = h[1];
     st.mu = h[2];
     st.omega = h[3];
     st.residual = h[4];
     st.density_error = h[5];
-    st.iterations = it + 1;
+    st.iterations = (int)h[6];
     if (!(st.residual == st.residual) || !(st.omega == st.omega) || st.residual > 1e300) {
       status = device_fault_status(ctx);
       if (status == KPM_OK) status = fail(ctx, KPM_ENONFINITE, "non-finite order parameters in the RMFT iteration");
@@ -691,6 +811,8 @@ int rmft_iterate(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     st.converged = st.residual < ropts->tol && fabs(st.density_error) < ropts->tol;
     if (st.converged) break;
   }
+  if (status == KPM_OK && ropts->strict && !st.converged && n_iter > 0)
+    status = fail(ctx, KPM_ENOTCONV, "rmft_iterate: tol not met within n_iter iterations");
   if (!params_dev) KPM_CU(cudaMemcpyAsync(params, dpar, 26 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!mu_dev) KPM_CU(cudaMemcpyAsync(mu_eff, dmu, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!params_dev || !mu_dev) KPM_CU(cudaStreamSynchronize(s));
@@ -729,9 +851,11 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   kpm_opts o = *opts;
   o.flags &= ~KPM_FLAG_DOUBLE_STEP;
   const size_t elem = o.precision == KPM_FP32 ? 8 : 16;
-  if (o.block_width == 0) {
+  // unit columns of the pass (all D, or those of the site range)
+  const int64_t ncol = (o.site_begin != 0 || o.site_end != 0) ? 2 * ((int64_t)o.site_end - o.site_begin) : D;
+  if (o.block_width == 0 && ncol > 0) {
     const int64_t fit = (int64_t)(ctx->budget / ((uint64_t)(nvec + 2) * D * elem));
-    o.block_width = (int)balanced_width(D, std::max<int64_t>(1, std::min<int64_t>(D, fit)));
+    o.block_width = (int)balanced_width(ncol, std::max<int64_t>(1, std::min<int64_t>(ncol, fit)));
   }
   PassPlan pp;
   if ((r = plan_pass(ctx, model, &o, &pp))) return r;
@@ -759,12 +883,14 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     KPM_CU(launch_scale_table_f32(*model, fields, ab, (float2*)ctx->table, s));
   else
     KPM_CU(launch_scale_table_f64(*model, fields, ab, (double2*)ctx->table, s));
-  KPM_CU(launch_seed_weights(model->nx, model->ny, grad_obs, ab, grad_omega, ctx->wseed, s));
+  // seeds of the columns outside the site range are zero: their backward
+  // vectors stay zero, so they add nothing where a slab runs past the range
+  KPM_CU(launch_seed_weights(model->nx, model->ny, grad_obs, ab, grad_omega, ctx->wseed, s, pp.sb, pp.se));
   KPM_CU(cudaMemsetAsync(Gpart, 0, gbytes * (size_t)groups, s));
   const double* am = ctx->am;
   const double* ao = ctx->ao;
 
-  for (int64_t s0 = 0; s0 < D && M >= 2; s0 += pp.width) {
+  for (int64_t s0 = pp.c0; s0 < pp.c1 && M >= 2; s0 += pp.width) {
     // forward, writing the checkpointed vectors (alpha_{k seg}, alpha_{k seg + 1})
     // in place and stepping through the two temporaries otherwise
     auto ckpt_slot = [&](int idx) -> void* {
@@ -845,6 +971,7 @@ int kpm_ldos(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const d
   if (!(gamma0 > 0.0) || !(gamma_alpha >= 0.0)) return fail(ctx, KPM_EINVAL, "need gamma0 > 0 and gamma_alpha >= 0");
   if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: the LDOS needs both Nambu rows");
   if (opts->precision == KPM_DF64) return fail(ctx, KPM_EINVAL, "KPM_DF64: not supported by kpm_ldos");
+  if (opts->site_begin || opts->site_end) return fail(ctx, KPM_EINVAL, "site range: not supported by kpm_ldos");
   DeviceGuard g(ctx->device);
   const int N = model->nx * model->ny;
   const int64_t D = 2 * (int64_t)N;
@@ -892,6 +1019,11 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
   if ((r = check_dev(ctx, mu_eff, "mu_eff"))) return r;
   if (opts->flags & KPM_FLAG_PH_HALF) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by the batched call");
   if (opts->probe_p) return fail(ctx, KPM_EINVAL, "probing: not supported by the batched call");
+  if (opts->site_begin || opts->site_end) return fail(ctx, KPM_EINVAL, "site range: not supported by the batched call");
+  for (int c = 0; c < ncell; ++c)
+    if ((r = check_rmft_opts(ctx, &ropts[c]))) return r;
+    else if (ropts[c].anderson || ropts[c].sync_every > 1)
+      return fail(ctx, KPM_EINVAL, "the batched call mixes linearly and reads every iteration");
   if (opts->M < 1 || (opts->precision != KPM_FP32 && opts->precision != KPM_FP64))
     return fail(ctx, KPM_EINVAL, "bad opts");
   DeviceGuard g(ctx->device);
@@ -1206,6 +1338,7 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     for (int c : cols) for (int mode : modes) {
       kpm_opts o = *opts;
       o.M = Mt;
+      o.site_begin = o.site_end = 0;
       o.block_width = (int)w;
       o.cols_per_block = c;
       o.flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | mode;

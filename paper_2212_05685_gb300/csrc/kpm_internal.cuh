@@ -91,14 +91,29 @@ cudaError_t launch_scale_table_df(const kpm_model& m, const double* fields, cons
 cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, const double* ab,
                                    double2* table, cudaStream_t s);
 // obs from accumulators; omega = a * sum Re acc[J][9] (if omega != null)
-// half: particle-hole half pass (only the columns (j, up) accumulated)
+// half: particle-hole half pass (only the columns (j, up) accumulated);
+// sites outside [sb, se) (se < 0: N) get zeros and no Omega part
 cudaError_t launch_assemble(int nx, int ny, const double2* acc, const double* ab, double* obs, double* omega,
-                            double* red, cudaStream_t s, int half = 0);
+                            double* red, cudaStream_t s, int half = 0, int sb = 0, int se = -1);
 // sum of a device array into *out (deterministic two-stage reduction)
 cudaError_t launch_sum(const double* x, int64_t n, double* out, double* red, cudaStream_t s);
-// RMFT mixing update; writes stats4 = {residual, density_error, -, -} and updates mu_eff
+// Anderson mixing state (device): history ring dX, dF (m x L), previous x and f,
+// current f (L each), Gram partials, gamma; L = 26 N + 1
+struct AndersonState {
+  int m = 0;
+  double *dX = nullptr, *dF = nullptr, *xprev = nullptr, *fprev = nullptr, *fcur = nullptr, *gpart = nullptr,
+         *gamma = nullptr;
+};
+size_t anderson_doubles(int N, int m);
+AndersonState anderson_state(int N, int m, double* base);
+// RMFT mixing update; writes stats = {residual, density_error} and updates mu_eff
+// (linear mixing, or Anderson mixing when an && an->m > 0); rec (optional, 16
+// doubles, rec[6..8] zero at the start of a call): record of the iteration,
+// snap = {a, b, mu, omega} of its pass; an iteration after one that met tol
+// changes nothing
 cudaError_t launch_update(int N, double* params, double* obs, double* mu_eff, const kpm_rmft_opts& o,
-                          double* stats, double* red, cudaStream_t s);
+                          double* stats, double* red, cudaStream_t s, double* rec = nullptr,
+                          const double* snap = nullptr, const AndersonState* an = nullptr);
 int reduce_scratch_doubles(int64_t n);
 
 // ---------------------------------------------------------------- cheb_kernels.cu
@@ -132,6 +147,10 @@ cudaError_t launch_cheb_step_batched(const ChebPlan& p, int ncell, const BatchPt
 // device fault word of the TMA-staged FP32 step (bit 0: a bounded wait
 // expired; bit 1: shared memory misaligned for TMA); sticky for the process
 cudaError_t read_step_fault(unsigned int* out);
+cudaError_t clear_step_fault();
+// failure-path test hook: the next drop_copies CTAs of the TMA step skip one
+// window copy; bounded-wait limit of later launches (0: the default 2 s)
+cudaError_t set_step_failure_test(int drop_copies, uint64_t wait_limit_ns);
 // table conj(xi_J) of the probing phases, J < D
 cudaError_t launch_probe_phases(const ChebPlan& p, double2* xi_conj, cudaStream_t s);
 // acc += a_m V[local rows] for the slab's columns (no recursion)
@@ -140,9 +159,10 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
                                cudaStream_t s);
 
 // ---------------------------------------------------------------- kpm_adjoint.cu
-// seed weights w[J][10] of every unit column from the upstream gradients
+// seed weights w[J][10] of every unit column from the upstream gradients (zero
+// for the columns of sites outside [sb, se), se < 0: N)
 cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const double* ab, double g_omega,
-                                double2* w, cudaStream_t s);
+                                double2* w, cudaStream_t s, int sb = 0, int se = -1);
 // lambda[K_s(J), c] += coef_s(m) w[J][s] over the slab's columns
 cudaError_t launch_seed_scatter(const ChebPlan& p, int prec, void* lam, int64_t s0, const double2* w,
                                 const double* am, const double* ao, int m, cudaStream_t s);
@@ -158,6 +178,12 @@ cudaError_t launch_grad_fields(int nx, int ny, const double2* G, const double* a
 // dL/dphi through the fields' dependence on the Peierls phases (rmft_kernels.cu)
 cudaError_t launch_phi_grad(const kpm_model& m, const double* phi, const double* params, const double* grad_fields,
                             double* grad_phi, cudaStream_t s);
+
+// ---------------------------------------------------------------- kpm_peaks.cu
+// FMA throughput of the FP64 and FP32 pipes: out = {FP64 TFLOP/s, FP32 TFLOP/s,
+// packed f32x2 TFLOP/s, median SM MHz}; scratch: peak_scratch_bytes(sms) device bytes
+size_t peak_scratch_bytes(int sms);
+cudaError_t measure_alu_peaks(int sms, void* scratch, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- kpm_ldos.cu
 // C[sigma][k][m] of the resolvent series (see kpm_ldos.cu)

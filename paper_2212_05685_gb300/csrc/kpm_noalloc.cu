@@ -12,9 +12,12 @@
 //
 // The array is part of the loaded module: every GPU that loads this library
 // holds kNoAllocScratchBytes of it until the process exits.  Its device
-// address is resolved once per device, by the first call made with that
-// device current (cudaGetSymbolAddress); make that first call before any
-// stream capture.  Every call on a device shares the one array, so calls
+// address is resolved with that device current (cudaGetSymbolAddress) by
+// every call made outside stream capture, so a module reloaded after a
+// context teardown (cudaDeviceReset) is found at its new address; a call made
+// while its stream captures reuses the address of the last call outside
+// capture on that device, so make one call before capturing.  Every call on a
+// device shares the one array, so calls
 // whose work overlaps on the GPU (different streams, or host threads racing)
 // corrupt each other's intermediates: serialise them.  Each call writes every
 // scratch byte it later reads, so nothing has to start at zero and a call
@@ -35,28 +38,35 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// device address of g_noalloc_scratch on `device` (current), resolved once
-cudaError_t scratch_address(int device, void** out) {
+// device address of g_noalloc_scratch on `device` (current): resolved afresh
+// unless `stream` is capturing, then the address of the last call outside
+// capture (cudaErrorNotReady when there was none)
+cudaError_t scratch_address(int device, cudaStream_t stream, void** out) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[device]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[device] = p;
   }
+  if (!g_scratch_addr[device]) return cudaErrorNotReady;
   *out = g_scratch_addr[device];
   return cudaSuccess;
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
-bool is_device(const void* p) {
+// device memory of GPU `dev` (or managed memory)
+bool is_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -70,13 +80,16 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
   if ((o->flags & KPM_FLAG_PH_HALF) || o->probe_p) return KPM_EINVAL;  // the exact full pass only
+  if (o->block_width < 0 || o->cols_per_block < 0) return KPM_EINVAL;
+  if (o->site_begin != 0 || o->site_end != 0) return KPM_EINVAL;      // all sites
   if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return KPM_EINVAL;
-  if (!is_device(fields) || !is_device(ab) || !is_device(obs) || (omega && !is_device(omega))) return KPM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return KPM_ECUDA;
   }
+  if (!is_device(fields, dev) || !is_device(ab, dev) || !is_device(obs, dev) || (omega && !is_device(omega, dev)))
+    return KPM_EINVAL;
   const int N = m->nx * m->ny;
   const int64_t D = 2 * (int64_t)N;
   const size_t elem = o->precision == KPM_FP32 ? 8 : 16;
@@ -105,7 +118,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (width < 1 || p.cb == 0) return KPM_EINVAL;  // not even one column chunk fits
 
   void* base = nullptr;
-  cudaError_t e = scratch_address(dev, &base);
+  cudaError_t e = scratch_address(dev, (cudaStream_t)stream, &base);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return KPM_ECUDA;

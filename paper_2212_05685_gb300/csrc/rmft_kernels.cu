@@ -521,12 +521,27 @@ __global__ void scale_table_kernel(kpm_model m, const double* __restrict__ fld, 
 // sector F_M(h~) = 1 - U conj(F_M(h~)) U^T (U: (c_up, c^dag_dn) -> (c_dn,
 // -c^dag_up) per site), so column (j,1) gives n_dn = n_up, chi_dn = chi_up, and
 // acc[(j,0)][9] already holds both diagonal Omega moments.
+// Sites outside [sb, se) (a pass over part of the columns) get zero order
+// parameters and add nothing to Omega.
 __global__ void assemble_kernel(int nx, int ny, const double2* __restrict__ acc, double* __restrict__ obs,
-                                double* __restrict__ part, int half) {
+                                double* __restrict__ part, int half, int sb, int se) {
   const int N = nx * ny;
   const Layout L{N};
   double om = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    if (j < sb || j >= se) {
+      for (int s = 0; s < 2; ++s) *L.n_ptr(obs, s, j) = 0.0;
+      for (int s = 0; s < 2; ++s)
+        for (int d = 0; d < 4; ++d) {
+          double* q = L.chi_ptr(obs, s, d, j);
+          q[0] = q[1] = 0.0;
+        }
+      for (int e = 0; e < 4; ++e) {
+        double* q = L.F_ptr(obs, e, j);
+        q[0] = q[1] = 0.0;
+      }
+      continue;
+    }
     const double2* a0 = acc + (size_t)(2 * j) * kSlots;
     const double2* a1 = acc + (size_t)(2 * j + 1) * kSlots;
     *L.n_ptr(obs, 0, j) = a0[0].x;
@@ -563,8 +578,16 @@ __global__ void assemble_kernel(int nx, int ny, const double2* __restrict__ acc,
 // Mixing update (readings R1, R2): part 1 per site for the densities
 // (paramagnetic average, projection onto <n> = n_target), part 2 for the
 // complex parameters.  Writes the per-block max |p_new - p| into part.
+// rec (optional): per-call record of the loop, {a, b, mu, omega, residual,
+// density error, iterations, frozen, ...}; once an iteration met tol (or
+// turned non-finite) `frozen` is set and later iterations leave every output
+// as it is, so queuing iterations past convergence changes nothing.
+__device__ __forceinline__ bool frozen(const double* rec) { return rec != nullptr && rec[7] != 0.0; }
+
 __global__ void update_kernel(int N, double* __restrict__ p, double* __restrict__ o,
-                              const double* __restrict__ nsum, kpm_rmft_opts opt, double* __restrict__ part) {
+                              const double* __restrict__ nsum, kpm_rmft_opts opt, double* __restrict__ part,
+                              const double* __restrict__ rec) {
+  if (frozen(rec)) return;
   const double e = *nsum / N - opt.n_target;
   double r = 0.0;
   const int64_t total = (int64_t)N + 24 * (int64_t)N;  // N site pairs, then 24N complex reals
@@ -593,8 +616,21 @@ __global__ void update_kernel(int N, double* __restrict__ p, double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
+// the record of one finished iteration: stats of its pass (snap = {a, b, mu,
+// omega}), residual r, density error e, count; freezes on tol or non-finite
+__device__ void record_iteration(double* rec, const double* snap, double r, double e, double tol) {
+  for (int k = 0; k < 4; ++k) rec[k] = snap[k];
+  rec[4] = r;
+  rec[5] = e;
+  rec[6] += 1.0;
+  const bool bad = !(r == r) || r > 1e300 || !(snap[3] == snap[3]);
+  if (bad || (r < tol && fabs(e) < tol)) rec[7] = 1.0;
+}
+
 __global__ void update_final(const double* __restrict__ part, int n, int N, const double* __restrict__ nsum,
-                             kpm_rmft_opts opt, double* __restrict__ mu_eff, double* __restrict__ stats) {
+                             kpm_rmft_opts opt, double* __restrict__ mu_eff, double* __restrict__ stats,
+                             double* __restrict__ rec, const double* __restrict__ snap) {
+  if (frozen(rec)) return;
   double r = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) r = fmax(r, part[k]);
   r = block_reduce<1>(r);
@@ -603,6 +639,166 @@ __global__ void update_final(const double* __restrict__ part, int n, int N, cons
     stats[0] = r;
     stats[1] = e;
     *mu_eff = *mu_eff - opt.eta * e;
+    if (rec) record_iteration(rec, snap, r, e, opt.tol);
+  }
+}
+
+// ---- Anderson (Pulay) mixing, reading R4 -----------------------------------
+// State x = (params, mu_eff) of length L = 26 N + 1; preconditioned residual
+// f = B (G(x) - x) with B the linear mixings (alpha_n on the densities, alpha
+// on chi and F) and f_mu = -eta e; history of the last m differences dX, dF
+// (ring, slot (k - 1) mod m at Anderson iteration k); gamma = argmin
+// |f - dF gamma|_2 with the normal equations regularised by 1e-10 tr/nh;
+// x <- x + f - (dX + dF) gamma.
+__global__ void anderson_resid_kernel(int N, const double* __restrict__ p, double* __restrict__ o,
+                                      const double* __restrict__ nsum, const double* __restrict__ mu_eff,
+                                      kpm_rmft_opts opt, int m, double* __restrict__ xprev, double* __restrict__ fprev,
+                                      double* __restrict__ fcur, double* __restrict__ dX, double* __restrict__ dF,
+                                      double* __restrict__ part, const double* __restrict__ rec) {
+  if (frozen(rec)) return;
+  const double e = *nsum / N - opt.n_target;
+  const int k = (int)rec[8];
+  const int64_t L = 26 * (int64_t)N + 1;
+  const int64_t slot = k >= 1 ? (int64_t)((k - 1) % m) * L : -1;
+  double r = 0.0;
+  auto put = [&](int64_t q, double x, double f) {
+    if (slot >= 0) {
+      dX[slot + q] = x - xprev[q];
+      dF[slot + q] = f - fprev[q];
+    }
+    xprev[q] = x;
+    fprev[q] = f;
+    fcur[q] = f;
+  };
+  const int64_t items = (int64_t)N + 24 * (int64_t)N + 1;  // N site pairs, 24 N complex reals, mu_eff
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < items; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < N) {
+      const int i = (int)t;
+      double ou = o[i], od = o[N + i];
+      if (opt.paramagnetic) ou = od = 0.5 * (ou + od);
+      ou -= 0.5 * e;
+      od -= 0.5 * e;
+      const double pu = p[i], pd = p[N + i];
+      r = fmax(r, fmax(fabs(ou - pu), fabs(od - pd)));
+      o[i] = ou;
+      o[N + i] = od;
+      put(i, pu, opt.alpha_n * (ou - pu));
+      put(N + i, pd, opt.alpha_n * (od - pd));
+    } else if (t < items - 1) {
+      const int64_t q = 2 * (int64_t)N + (t - N);
+      const double pv = p[q], ov = o[q];
+      r = fmax(r, fabs(ov - pv));
+      put(q, pv, opt.alpha * (ov - pv));
+    } else {
+      put(L - 1, *mu_eff, -opt.eta * e);
+    }
+  }
+  r = block_reduce<1>(r != r ? INFINITY : r);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+constexpr int kAndChunks = 16;  // column chunks of the Gram sums
+
+// partial dot products: blockIdx.x = pair (a, b) with a <= b < m, or (a, m)
+// for <dF_a, f>; blockIdx.y = chunk of the L entries
+__global__ void anderson_gram_kernel(int64_t L, int m, const double* __restrict__ dF, const double* __restrict__ fcur,
+                                     double* __restrict__ gpart, const double* __restrict__ rec) {
+  if (frozen(rec)) return;
+  int a = 0, b = 0, t = blockIdx.x;
+  for (a = 0; a < m; ++a) {
+    const int row = m + 1 - a;  // pairs (a, a..m)
+    if (t < row) {
+      b = a + t;
+      break;
+    }
+    t -= row;
+  }
+  const double* u = dF + (int64_t)a * L;
+  const double* v = b < m ? dF + (int64_t)b * L : fcur;
+  const int64_t chunk = (L + kAndChunks - 1) / kAndChunks;
+  const int64_t lo = blockIdx.y * chunk, hi = min(L, lo + chunk);
+  double acc = 0.0;
+  for (int64_t q = lo + threadIdx.x; q < hi; q += blockDim.x) acc += u[q] * v[q];
+  acc = block_reduce<0>(acc);
+  if (threadIdx.x == 0) gpart[(int64_t)blockIdx.x * kAndChunks + blockIdx.y] = acc;
+}
+
+// gamma from the regularised normal equations (Cholesky, nh <= 16 unknowns);
+// gamma = 0 when there is no history or the factorisation fails
+__global__ void anderson_solve_kernel(int m, const double* __restrict__ gpart, double* __restrict__ gamma,
+                                      const double* __restrict__ rec) {
+  if (frozen(rec) || threadIdx.x != 0) return;
+  const int nh = min((int)rec[8], m);
+  double G[16][16], rhs[16];
+  int t = 0;
+  for (int a = 0; a < m; ++a)
+    for (int b = a; b <= m; ++b, ++t) {
+      double v = 0.0;
+      for (int c = 0; c < kAndChunks; ++c) v += gpart[(int64_t)t * kAndChunks + c];
+      if (a < nh && b < nh) G[a][b] = G[b][a] = v;
+      if (a < nh && b == m) rhs[a] = v;
+    }
+  for (int a = 0; a < m; ++a) gamma[a] = 0.0;
+  if (nh == 0) return;
+  double tr = 0.0;
+  for (int a = 0; a < nh; ++a) tr += G[a][a];
+  if (!(tr > 0.0) || !(tr < 1e300)) return;
+  const double reg = 1e-10 * tr / nh;
+  for (int a = 0; a < nh; ++a) G[a][a] += reg;
+  // Cholesky G = C C^T in place (lower triangle)
+  for (int j = 0; j < nh; ++j) {
+    double d = G[j][j];
+    for (int k = 0; k < j; ++k) d -= G[j][k] * G[j][k];
+    if (!(d > 0.0)) return;
+    const double cjj = sqrt(d);
+    G[j][j] = cjj;
+    for (int i = j + 1; i < nh; ++i) {
+      double v = G[i][j];
+      for (int k = 0; k < j; ++k) v -= G[i][k] * G[j][k];
+      G[i][j] = v / cjj;
+    }
+  }
+  double y[16];
+  for (int i = 0; i < nh; ++i) {
+    double v = rhs[i];
+    for (int k = 0; k < i; ++k) v -= G[i][k] * y[k];
+    y[i] = v / G[i][i];
+  }
+  for (int i = nh - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < nh; ++k) v -= G[k][i] * gamma[k];
+    gamma[i] = v / G[i][i];
+  }
+}
+
+__global__ void anderson_apply_kernel(int N, double* __restrict__ p, double* __restrict__ mu_eff, int m,
+                                      const double* __restrict__ fcur, const double* __restrict__ dX,
+                                      const double* __restrict__ dF, const double* __restrict__ gamma,
+                                      const double* __restrict__ rec) {
+  if (frozen(rec)) return;
+  const int64_t L = 26 * (int64_t)N + 1;
+  const int nh = min((int)rec[8], m);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L; q += (int64_t)gridDim.x * blockDim.x) {
+    double* x = q < L - 1 ? p + q : mu_eff;
+    double v = *x + fcur[q];
+    for (int a = 0; a < nh; ++a) v -= gamma[a] * (dX[(int64_t)a * L + q] + dF[(int64_t)a * L + q]);
+    *x = v;
+  }
+}
+
+__global__ void anderson_final(const double* __restrict__ part, int n, int N, const double* __restrict__ nsum,
+                               kpm_rmft_opts opt, double* __restrict__ stats, double* __restrict__ rec,
+                               const double* __restrict__ snap) {
+  if (frozen(rec)) return;
+  double r = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) r = fmax(r, part[k]);
+  r = block_reduce<1>(r);
+  if (threadIdx.x == 0) {
+    const double e = *nsum / N - opt.n_target;
+    stats[0] = r;
+    stats[1] = e;
+    rec[8] += 1.0;
+    record_iteration(rec, snap, r, e, opt.tol);
   }
 }
 
@@ -836,9 +1032,9 @@ cudaError_t launch_scale_table_f64(const kpm_model& m, const double* fields, con
 }
 
 cudaError_t launch_assemble(int nx, int ny, const double2* acc, const double* ab, double* obs, double* omega,
-                            double* red, cudaStream_t s, int half) {
+                            double* red, cudaStream_t s, int half, int sb, int se) {
   const int g = grid_for(nx * ny);
-  assemble_kernel<<<g, kRedBlock, 0, s>>>(nx, ny, acc, obs, red, half);
+  assemble_kernel<<<g, kRedBlock, 0, s>>>(nx, ny, acc, obs, red, half, sb, se < 0 ? nx * ny : se);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess || omega == nullptr) return err;
   // omega = a * sum Re acc[J][9]; a read on the device
@@ -847,14 +1043,48 @@ cudaError_t launch_assemble(int nx, int ny, const double2* acc, const double* ab
 }
 
 cudaError_t launch_update(int N, double* params, double* obs, double* mu_eff, const kpm_rmft_opts& o,
-                          double* stats, double* red, cudaStream_t s) {
+                          double* stats, double* red, cudaStream_t s, double* rec, const double* snap,
+                          const AndersonState* an) {
   double* nsum = red + 2 * kRedGrid + 8;
   cudaError_t err = launch_sum(obs, 2 * (int64_t)N, nsum, red, s);
   if (err != cudaSuccess) return err;
-  const int g = grid_for(25 * (int64_t)N);
-  update_kernel<<<g, kRedBlock, 0, s>>>(N, params, obs, nsum, o, red);
-  update_final<<<1, kRedBlock, 0, s>>>(red, g, N, nsum, o, mu_eff, stats);
+  if (an == nullptr || an->m < 1) {
+    const int g = grid_for(25 * (int64_t)N);
+    update_kernel<<<g, kRedBlock, 0, s>>>(N, params, obs, nsum, o, red, rec);
+    update_final<<<1, kRedBlock, 0, s>>>(red, g, N, nsum, o, mu_eff, stats, rec, snap);
+    return cudaGetLastError();
+  }
+  const int m = an->m;
+  const int64_t L = 26 * (int64_t)N + 1;
+  const int g = grid_for(25 * (int64_t)N + 1);
+  anderson_resid_kernel<<<g, kRedBlock, 0, s>>>(N, params, obs, nsum, mu_eff, o, m, an->xprev, an->fprev, an->fcur,
+                                                an->dX, an->dF, red, rec);
+  const int pairs = m * (m + 3) / 2;  // (a, b) with a <= b < m, and (a, f)
+  anderson_gram_kernel<<<dim3(pairs, kAndChunks), kRedBlock, 0, s>>>(L, m, an->dF, an->fcur, an->gpart, rec);
+  anderson_solve_kernel<<<1, 32, 0, s>>>(m, an->gpart, an->gamma, rec);
+  anderson_apply_kernel<<<grid_for(L), kRedBlock, 0, s>>>(N, params, mu_eff, m, an->fcur, an->dX, an->dF, an->gamma,
+                                                          rec);
+  anderson_final<<<1, kRedBlock, 0, s>>>(red, g, N, nsum, o, stats, rec, snap);
   return cudaGetLastError();
+}
+
+size_t anderson_doubles(int N, int m) {
+  const size_t L = 26 * (size_t)N + 1;
+  return (2 * (size_t)m + 3) * L + (size_t)(m * (m + 3) / 2) * kAndChunks + 16;
+}
+
+AndersonState anderson_state(int N, int m, double* base) {
+  const size_t L = 26 * (size_t)N + 1;
+  AndersonState a;
+  a.m = m;
+  a.dX = base;
+  a.dF = base + (size_t)m * L;
+  a.xprev = base + 2 * (size_t)m * L;
+  a.fprev = a.xprev + L;
+  a.fcur = a.fprev + L;
+  a.gpart = a.fcur + L;
+  a.gamma = a.gpart + (size_t)(m * (m + 3) / 2) * kAndChunks;
+  return a;
 }
 
 }  // namespace kpm

@@ -38,13 +38,14 @@ class kpm_opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("precision", ctypes.c_int32), ("block_width", ctypes.c_int32),
                 ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double), ("temperature", ctypes.c_double),
                 ("flags", ctypes.c_int32),
-                ("probe_p", ctypes.c_int32), ("probe_seed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("probe_p", ctypes.c_int32), ("probe_seed", ctypes.c_int32), ("site_begin", ctypes.c_int32),
+                ("site_end", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class kpm_rmft_opts(ctypes.Structure):
     _fields_ = [("n_target", ctypes.c_double), ("alpha", ctypes.c_double), ("alpha_n", ctypes.c_double),
                 ("eta", ctypes.c_double), ("tol", ctypes.c_double), ("paramagnetic", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("strict", ctypes.c_int32), ("anderson", ctypes.c_int32), ("sync_every", ctypes.c_int32)]
 
 
 class kpm_rmft_stats(ctypes.Structure):
@@ -61,6 +62,11 @@ _SIGNATURES = {
     "kpm_destroy": (ctypes.c_int, [_P]),
     "kpm_set_scratch_budget": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "kpm_sync_status": (ctypes.c_int, [_P, _P]),
+    "kpm_inject_lost_copy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "kpm_measure_peaks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _P]),
+    "rmft_prepare": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_opts), _P, _P, _P, _P, _P, _P,
+                                    _P]),
+    "rmft_update": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), ctypes.POINTER(kpm_rmft_opts), _P, _P, _P, _P, _P]),
     "kpm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kpm_last_error": (ctypes.c_char_p, [_P]),
     "kpm_peierls_phases": (ctypes.c_int, [_P, ctypes.POINTER(kpm_model), _P, _P]),
@@ -139,12 +145,15 @@ def make_model(nx, ny, t=1.0, tp=-0.3, J=0.3, flux=1, gutzwiller=True):
 
 
 def make_opts(M, precision=KPM_FP32, block_width=0, cols_per_block=0, margin=0.01, flags=0, probe_p=0,
-              probe_seed=0, temperature=0.0):
-    return kpm_opts(M, precision, block_width, cols_per_block, margin, temperature, flags, probe_p, probe_seed, 0)
+              probe_seed=0, temperature=0.0, site_begin=0, site_end=0):
+    return kpm_opts(M, precision, block_width, cols_per_block, margin, temperature, flags, probe_p, probe_seed,
+                    site_begin, site_end, 0)
 
 
-def make_rmft_opts(n_target, alpha=0.5, alpha_n=0.05, eta=0.5, tol=1e-7, paramagnetic=True):
-    return kpm_rmft_opts(n_target, alpha, alpha_n, eta, tol, 1 if paramagnetic else 0, 0)
+def make_rmft_opts(n_target, alpha=0.5, alpha_n=0.05, eta=0.5, tol=1e-7, paramagnetic=True, strict=False,
+                   anderson=0, sync_every=0):
+    return kpm_rmft_opts(n_target, alpha, alpha_n, eta, tol, 1 if paramagnetic else 0, 1 if strict else 0,
+                         int(anderson), int(sync_every))
 
 
 class Context:
@@ -191,6 +200,29 @@ def kpm_set_scratch_budget(ctx: Context, nbytes: int):
 
 def kpm_sync_status(ctx: Context, stream=None):
     return ctx.check(ctx.lib.kpm_sync_status(ctx.handle, _stream(stream)), "kpm_sync_status")
+
+
+def kpm_inject_lost_copy(ctx: Context, count, wait_limit_s=0.0):
+    return ctx.check(ctx.lib.kpm_inject_lost_copy(ctx.handle, int(count), float(wait_limit_s)),
+                     "kpm_inject_lost_copy")
+
+
+def kpm_measure_peaks(ctx: Context, stream=None):
+    """(FP64 TFLOP/s, FP32 TFLOP/s, packed f32x2 TFLOP/s, median SM MHz)."""
+    out = (ctypes.c_double * 4)()
+    ctx.check(ctx.lib.kpm_measure_peaks(ctx.handle, out, _stream(stream)), "kpm_measure_peaks")
+    return tuple(out)
+
+
+def rmft_prepare(ctx: Context, model, opts, phi, params, mu_eff, fields, ab, mu_out, stream=None):
+    return ctx.check(ctx.lib.rmft_prepare(ctx.handle, ctypes.byref(model), ctypes.byref(opts), _ptr(phi),
+                                          _ptr(params), _ptr(mu_eff), _ptr(fields), _ptr(ab), _ptr(mu_out),
+                                          _stream(stream)), "rmft_prepare")
+
+
+def rmft_update(ctx: Context, model, ropts, params, obs, mu_eff, stats_out, stream=None):
+    return ctx.check(ctx.lib.rmft_update(ctx.handle, ctypes.byref(model), ctypes.byref(ropts), _ptr(params),
+                                         _ptr(obs), _ptr(mu_eff), _ptr(stats_out), _stream(stream)), "rmft_update")
 
 
 def kpm_peierls_phases(ctx: Context, model, phi, stream=None):

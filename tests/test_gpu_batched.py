@@ -87,3 +87,45 @@ def test_batched_cell_follows_oracle(K):
     assert np.max(np.abs(params[k].cpu().numpy() - p)) < 1e-10
     assert float(mu[k].item()) == pytest.approx(mu_eff, abs=1e-10)
     kpm.kpm_destroy(ctx)
+
+
+def test_batched_cfg3_shapes_follow_oracle(K):
+    """One cell of each shape of the 32-cell mix (24x12, 32x16, 48x24, 64x32;
+    doping and seeds as drawn by cfg3_cells), FP32 at M = 1024 as benchmarked,
+    one batched iteration: every site's updated n, chi, F, the residual and
+    the density error against the oracle's shifted_fields -> f_spectral ->
+    update chain (FP32 tolerance 2e-5)."""
+    kpm = K
+    cells = inputs.cfg3_cells(seed=0, count=32)
+    pick = {}
+    for w in cells:
+        pick.setdefault((w.nx, w.ny), w)
+    assert sorted(pick) == [(24, 12), (32, 16), (48, 24), (64, 32)]
+    ws = [pick[s] for s in sorted(pick)]
+    ctx = kpm.kpm_create(0)
+    models, phis, params = [], [], []
+    for w in ws:
+        m = kpm.make_model(w.nx, w.ny)
+        phi = torch.empty(4 * w.n_sites, dtype=torch.float64, device="cuda")
+        kpm.kpm_peierls_phases(ctx, m, phi)
+        models.append(m)
+        phis.append(phi)
+        params.append(torch.tensor(inputs.vortex_seed(w), device="cuda"))
+    ropts = [kpm.make_rmft_opts(w.n_target, tol=0.0) for w in ws]
+    mu = torch.zeros(len(ws), dtype=torch.float64, device="cuda")
+    _, stats = kpm.rmft_iterate_batched(ctx, models, kpm.make_opts(1024, kpm.KPM_FP32), ropts, phis, params, mu, 1)
+    torch.cuda.synchronize()
+    for k, w in enumerate(ws):
+        om = rmft.Model(w.nx, w.ny)
+        p0 = inputs.vortex_seed(w)
+        f, mu_phys = rmft.shifted_fields(om, p0, 0.0)
+        a, b = bdg.gershgorin(om, f)
+        F1, omega = okpm.f_spectral(bdg.dense(om, f), a, b, w.M)
+        p1, mu1, r, e = rmft.update(p0, okpm.observables(om, F1), w.n_target, 0.0)
+        got = params[k].cpu().numpy()
+        assert np.max(np.abs(got - p1)) < 2e-5, (w.nx, w.ny)
+        assert stats[k].residual == pytest.approx(r, abs=2e-5)
+        assert stats[k].density_error == pytest.approx(e, abs=2e-5)
+        assert stats[k].omega == pytest.approx(omega, rel=1e-5)
+        assert float(mu[k].item()) == pytest.approx(mu1, abs=1e-5)
+    kpm.kpm_destroy(ctx)

@@ -50,7 +50,7 @@ def test_lbfgs_reaches_the_fixed_point():
     target = max(probf.last_residual, 1e-9)
     theta, obs, info = lbfgs.rmft_lbfgs(ctx, model, opts, phi, p0, mu_phys, max_iter=300, tol=target)
     print("fixed point iters", fp_iters, "fp field residual", target, "lbfgs", info, "start residual", res0)
-    # the adjoint accumulates G with atomics, so the trajectory varies run to run: ask for 200x
+    # the line search ends at the FP64 noise of the residual objective: ask for a 200x reduction
     assert info["field_residual"] < 5e-3 * res0
     start_dist = float((torch.tensor(inputs.uniform_dwave(nx, ny, 0.125), device="cuda") - p).abs().max())
     assert float((obs - p).abs().max()) < 1e-2 * start_dist

@@ -236,29 +236,33 @@ def test_full_size_uniform_against_momentum_space(K, prec, M, tol):
 
 def test_full_size_vortex_sampled_columns(K):
     """100 x 100 two-vortex cell with the PDW seed, M = 2048, FP32 as benchmarked:
-    sites sampled across the lattice against the oracle's recursion on their columns."""
+    112 sites (224 unit columns) against the oracle's recursion on their columns:
+    both vortex cores with their neighbours, four corners of the cell, and
+    sites drawn across the lattice (oracle columns on spawn-started processes)."""
+    import os
+    from oracle import pool
     kpm, _ = K
     w = inputs.CFG2
-    nx, ny = w.nx, w.ny
+    nx, ny, N = w.nx, w.ny, w.n_sites
     p = inputs.vortex_seed(w)
     model, _, fields, _ = gpu_fields(K, nx, ny, p, 0.0)
     obs, om, ab = gpu_pass(K, model, fields, w.M, kpm.KPM_FP32)
     orm = rmft.Model(nx, ny)
-    f = rmft.fields(orm, p, 0.0)
-    a, b = bdg.gershgorin(orm, f)
+    a, b = bdg.gershgorin(orm, rmft.fields(orm, p, 0.0))
     assert ab == pytest.approx([a, b], rel=1e-13)
-    rng = np.random.default_rng(5)
-    sites = np.concatenate([[0, nx - 1, nx * ny - 1, 25 + 50 * nx], rng.choice(nx * ny, 4, replace=False)])
-    cols = np.sort(np.concatenate([2 * sites, 2 * sites + 1]))
-    Fc, _ = okpm.f_naive(bdg.csr(orm, f), a, b, w.M, cols=cols)
-    full = np.zeros((2 * nx * ny, 2 * nx * ny), dtype=np.complex128, order="F")
-    full[:, cols] = Fc
-    ref = okpm.observables(orm, full)
-    gn, gc, gF = rmft.split(obs, nx * ny)
-    rn, rc, rF = rmft.split(ref, nx * ny)
-    assert np.max(np.abs(gn[:, sites] - rn[:, sites])) < FP32_TOL
-    assert np.max(np.abs(gc[:, :, sites] - rc[:, :, sites])) < FP32_TOL
-    assert np.max(np.abs(gF[:, sites] - rF[:, sites])) < FP32_TOL
+    sites = pool.sample_sites(nx, ny, 108, w.vortices, seed=5)
+    sites = np.unique(np.concatenate([sites, [0, nx - 1, N - nx, N - 1]]))
+    assert len(sites) >= 100
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    cp = pool.ColumnPool(nx, ny, p, 0.0, w.M, workers)
+    try:
+        rn, rc, rF, _ = cp.site_observables(sites)
+    finally:
+        cp.close()
+    gn, gc, gF = rmft.split(obs, N)
+    assert np.max(np.abs(gn[:, sites] - rn)) < FP32_TOL
+    assert np.max(np.abs(gc[:, :, sites] - rc)) < FP32_TOL
+    assert np.max(np.abs(gF[:, sites] - rF)) < FP32_TOL
 
 
 def test_invalid_arguments_are_refused(K):

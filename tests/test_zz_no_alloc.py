@@ -7,14 +7,18 @@ The allocation-free entry point keeps its intermediates in a fixed 48 MiB
 device array of the library.  This file checks, through the C ABI, that two
 calls in a row reproduce the context-based kpm_observables within the parity
 tolerances (FP64 1e-10, FP32 2e-5), on a lattice whose recursion slabs do not
-fit the array at once (so the entry point narrows them), and that oversized
-problems and host buffers are refused.  It runs last (file name) so that a
+fit the array at once (so the entry point narrows them), that on a small
+lattice both calls agree with the CPU oracle's spectral KPM (App. B) within
+the same tolerances, and that oversized problems, host buffers and negative
+slab widths are refused.  It runs last (file name) so that a
 failure here never hides the other GPU tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+from oracle import bdg, kpm as okpm, rmft
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -85,3 +89,35 @@ def test_refuses_what_does_not_fit_and_host_buffers(env):
     assert kpm.kpm_observables_noalloc(model, kpm.make_opts(16, 1), fields, ab2, out) == kpm.KPM_OK
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 2e-5), (0, 1e-10)])
+def test_two_calls_match_oracle(env, prec, tol):
+    kpm, inputs, ctx = env
+    nx, ny, M = 10, 8, 64
+    N = nx * ny
+    model, fields, ab = _fields(kpm, inputs, ctx, nx, ny)
+    w = inputs.Workload(nx, ny, 0.15, inputs.two_vortex(nx, ny), 64, seed=3)
+    om = rmft.Model(nx, ny)
+    f = rmft.fields(om, inputs.vortex_seed(w), 0.1)
+    a, b = bdg.gershgorin(om, f)
+    F1, omega = okpm.f_spectral(bdg.dense(om, f), a, b, M)
+    ref = okpm.observables(om, F1)
+    for call in range(2):
+        out = torch.full((26 * N,), float("nan"), dtype=torch.float64, device="cuda")
+        o = torch.empty(1, dtype=torch.float64, device="cuda")
+        assert kpm.kpm_observables_noalloc(model, kpm.make_opts(M, prec), fields, ab, out, o) == kpm.KPM_OK
+        torch.cuda.synchronize()
+        assert np.max(np.abs(out.cpu().numpy() - ref)) < tol, f"call {call}"
+        assert float(o.item()) == pytest.approx(omega, rel=1e-5 if prec == 1 else 1e-11)
+
+
+def test_refuses_negative_widths(env):
+    kpm, inputs, ctx = env
+    model, fields, ab = _fields(kpm, inputs, ctx, 6, 4)
+    out = torch.empty(26 * 24, dtype=torch.float64, device="cuda")
+    assert kpm.kpm_observables_noalloc(model, kpm.make_opts(16, 1, block_width=-1), fields, ab, out) == kpm.KPM_EINVAL
+    assert kpm.kpm_observables_noalloc(model, kpm.make_opts(16, 1, cols_per_block=-2), fields, ab, out) == \
+        kpm.KPM_EINVAL
+    assert kpm.kpm_observables_noalloc(model, kpm.make_opts(16, 1, site_begin=1, site_end=3), fields, ab, out) == \
+        kpm.KPM_EINVAL
