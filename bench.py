@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-cols", type=int, default=4, help="oracle columns per worker per step")
+    ap.add_argument("--error-sites", type=int, default=112,
+                    help="sites (two unit columns each) of the FP32-error and CPU-baseline sample")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -155,40 +157,18 @@ class Clocks:
 
 # ----------------------------------------------------------------------------- oracle sample (CPU)
 
-_W = {}
-
-
-def _worker_init(nx, ny, seed, M):
-    from oracle import bdg, rmft
-    from paper_2212_05685_gb300 import inputs
-    w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), M, seed=seed, pdw=0.02)
-    model = rmft.Model(nx, ny)
-    f = rmft.fields(model, inputs.vortex_seed(w), 0.0)
-    a, b = bdg.gershgorin(model, f)
-    _W.update(h=bdg.csr(model, f), a=a, b=b, M=M)
-
-
-def _worker_run(cols):
-    from oracle import kpm
-    t0 = time.perf_counter()
-    kpm.f_naive(_W["h"], _W["a"], _W["b"], _W["M"], cols=cols)
-    return time.perf_counter() - t0
-
-
 class OracleSample:
-    """The oracle's naive KPM (scipy CSR x unit-vector block, FP64) on a column
-    sample of the benchmark pass, one spawn-started process per host core."""
+    """The oracle's naive KPM (scipy CSR x unit-vector block, FP64) on a sample
+    of the benchmark pass's unit columns, one spawn-started process per host
+    core (oracle/pool.py), on the seed Hamiltonian of the benchmark cell."""
 
     def __init__(self, cols_per_worker, workers=None):
-        import multiprocessing as mp
+        from oracle import pool
         from paper_2212_05685_gb300 import inputs
         self.w = inputs.CFG2
         self.workers = workers or len(os.sched_getaffinity(0))
         self.cols = cols_per_worker
-        ctx = mp.get_context("spawn")
-        self.pool = ctx.Pool(self.workers, initializer=_worker_init,
-                             initargs=(self.w.nx, self.w.ny, self.w.seed, self.w.M))
-        self.pool.map(_worker_run, [[0]] * self.workers)  # warm the workers
+        self.pool = pool.ColumnPool(self.w.nx, self.w.ny, inputs.vortex_seed(self.w), 0.0, self.w.M, self.workers)
         self.rng = 0
 
     def step(self):
@@ -198,15 +178,21 @@ class OracleSample:
             start = (self.rng * 7919 + k * 1013) % (D - self.cols)
             jobs.append(list(range(start, start + self.cols)))
         self.rng += 1
-        t0 = time.perf_counter()
-        self.pool.map(_worker_run, jobs)
-        dt = time.perf_counter() - t0
+        dt = self.pool.time_columns(jobs)
         n = self.workers * self.cols
         return dt, n * self.w.M / dt, n
 
+    def sites(self, count):
+        """Order parameters of `count` sampled sites (both vortex cores with
+        their neighbours, the rest drawn across the cell) from their 2 count
+        columns, and the wall time."""
+        from oracle import pool
+        sites = pool.sample_sites(self.w.nx, self.w.ny, count, self.w.vortices, seed=5)
+        n, chi, F, dt = self.pool.site_observables(sites)
+        return sites, n, chi, F, dt
+
     def close(self):
         self.pool.close()
-        self.pool.join()
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -312,6 +298,16 @@ def run_ours(args):
                 "trial_ms_per_step": ms_step, "tuning_s": time.perf_counter() - t0}
         del f0, ab0
 
+    # the benchmarked pass on the seed Hamiltonian: its FP32 error is checked
+    # against the oracle's columns in the CPU-baseline leg
+    seed_pass = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    fs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    abs_ = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fs)
+    kpm.kpm_bounds(ctx, model, fs, 0.01, abs_)
+    kpm.kpm_observables(ctx, model, opts, fs, abs_, seed_pass)
+    del fs, abs_
+
     for _ in range(args.warmup):
         kpm.rmft_iterate(ctx, model, opts, ropts, phi, params, mu, 1)
     torch.cuda.synchronize()
@@ -389,6 +385,15 @@ def run_ours(args):
     traffic = measured_traffic("cheb_step2_fp32_100x100.json" if dbl else "cheb_step_fp32_100x100.json",
                                kernel_hash(), ldv) if 2 * D * ldv * 8 > 129e6 else None
 
+    # measured FMA rates of the FP64 and FP32 pipes (the ALU-bound rooflines)
+    alu = kpm.kpm_measure_peaks(ctx)
+    alu_peaks = {"fp64_tflops": alu[0], "fp32_tflops": alu[1], "fp32x2_tflops": alu[2], "sm_mhz": alu[3],
+                 "how": "independent FMA chains (8 per thread, 4 x 256 threads per SM), best of 3 launches, "
+                        "CUDA events (kpm_measure_peaks)"}
+    props = torch.cuda.get_device_properties(0)
+    sm_count = props.multi_processor_count
+    sm_mhz_run = (clk or {}).get("sm_mhz") or alu[3]
+
     fp64 = None
     if not args.no_fp64:
         # FP64 recursion at M = 128, scaled to M = 2048 (cost is linear in M)
@@ -409,13 +414,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         t64 = a0.elapsed_time(a1) / 1e3 * (M - 1) / (Ms - 1)
         # FP64 step: 13 complex multiply-adds and one complex subtraction per
-        # row-column (106 flops) against the nominal 1.25 TFLOP/s FP64 rate
+        # row-column (106 flops) against the measured FP64 FMA rate
         fp64_tflops = 106.0 * D * D * (M - 1) / t64 / 1e12
-        fp64 = {"s_per_pass": t64, "vector_moments_per_s": D * M / t64,
-                "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": 1.25, "unit": "TFLOP/s",
-                             "frac": fp64_tflops / 1.25, "peak_kind": "nominal FP64 rate"},
-                "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1)",
-                "fp32_speedup": t64 / (t / args.steps)}
+        # one RMFT iteration = the pass + the O(N) work around it, taken from
+        # the FP32 iteration (its time minus its recursion steps)
+        other = t / args.steps - rec_ms / 1e3 / args.steps
+        fp64 = {"s_per_pass": t64, "s_per_rmft_iteration": t64 + other, "vector_moments_per_s": D * M / t64,
+                "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": alu[0], "unit": "TFLOP/s",
+                             "frac": fp64_tflops / alu[0], "peak_kind": "measured FP64 FMA rate (kpm_measure_peaks)",
+                             "nominal_peak": 1.25},
+                "sample": f"FP64 pass at M={Ms} on the same cell, scaled by (M-1)/({Ms}-1): every step does the "
+                          f"same work, so the pass time is linear in M",
+                "fp32_speedup": (t64 + other) / (t / args.steps)}
 
     # double-float recursion (FP64-accurate, FP32 pipes) at M = 128, scaled
     # to M = 2048 like the FP64 line; its error against FP64 is in fp32_error
@@ -439,13 +449,16 @@ def run_ours(args):
         tdf = a0.elapsed_time(a1) / 1e3 * (M - 1) / (Ms - 1)
         # double-float step: 50 double-float multiply-adds of 12 FP32 operations
         # and two renormalisations of 6 per row-column (an FMA counted once),
-        # against the FP32 lane rate 152 SMs x 128 lanes x 2.07 GHz
+        # against the measured FP32 FMA rate in FMAs per second (scalar FMA,
+        # the kernel's instruction form)
         df_tops = 612.0 * D * D * (M - 1) / tdf / 1e12
-        lane_peak = 152 * 128 * 2.07e9 / 1e12
-        df64 = {"s_per_pass": tdf, "vector_moments_per_s": D * M / tdf,
+        lane_peak = alu[1] / 2.0
+        other = t / args.steps - rec_ms / 1e3 / args.steps
+        df64 = {"s_per_pass": tdf, "s_per_rmft_iteration": tdf + other, "vector_moments_per_s": D * M / tdf,
                 "roofline": {"bound": "alu", "achieved": df_tops, "peak": lane_peak,
                              "unit": "T FP32 lane operations/s", "frac": df_tops / lane_peak,
-                             "peak_kind": "nominal FP32 lane rate at the maximum SM clock"},
+                             "peak_kind": "measured FP32 FMA rate (kpm_measure_peaks), FMAs per second",
+                             "nominal_peak_at_run_clock": sm_count * 128 * sm_mhz_run * 1e6 / 1e12},
                 "fp64_equivalent_tflops": 106.0 * D * D * (M - 1) / tdf / 1e12,
                 "fp64_nominal_tflops": 1.25,
                 "speedup_vs_fp64": (fp64["s_per_pass"] / tdf) if fp64 else None,
@@ -493,14 +506,28 @@ def run_ours(args):
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
     precision = precision_section(kpm, inputs, torch)
 
-    cpu = None
+    # CPU baseline: the oracle's naive recursion on a sample of this pass's
+    # unit columns (the seed Hamiltonian), which also gives the FP32 error of
+    # the benchmarked pass at those sites
+    cpu, fp32_err = None, None
     if not args.no_cpu_baseline and world == 1:
+        import numpy as np
         samp = OracleSample(args.sample_cols)
-        dt, v, n = samp.step()
+        sites, rn, rc, rF, dt = samp.sites(args.error_sites)
         samp.close()
-        cpu = {"value": v, "unit": UNIT, "cores": samp.workers, "kind": "oracle",
-               "sample": f"{n} of {D} unit columns of one pass (naive FP64 Chebyshev recursion, scipy CSR, "
-                         f"M={M}), {dt:.1f} s"}
+        ncol = 2 * len(sites)
+        cpu = {"value": ncol * M / dt, "unit": UNIT, "cores": samp.workers, "kind": "oracle",
+               "sample": f"{ncol} of {D} unit columns of one pass (the columns of {len(sites)} sampled sites; naive "
+                         f"FP64 Chebyshev recursion, scipy CSR, M={M}), {dt:.1f} s"}
+        gobs = seed_pass.cpu().numpy()
+        gn = gobs[:2 * N].reshape(2, N)[:, sites]
+        gc = gobs[2 * N:18 * N].view(np.complex128).reshape(2, 4, N)[:, :, sites]
+        gF = gobs[18 * N:].view(np.complex128).reshape(4, N)[:, sites]
+        fp32_err = {"cell": "100x100", "M": M, "reference": "oracle naive FP64 recursion on the same columns",
+                    "sites": len(sites), "columns": ncol,
+                    "sites_include": "both vortex cores and their four neighbours",
+                    "max_err_n": float(np.abs(gn - rn).max()), "max_err_chi": float(np.abs(gc - rc).max()),
+                    "max_err_F": float(np.abs(gF - rF).max()), "bound": 2e-5}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -524,7 +551,9 @@ def run_ours(args):
         "clocks": clk,
         "fp64": fp64,
         "df64": df64,
-        "fp32_error": precision,
+        "fp32_error": fp32_err,
+        "fp32_error_48x24": precision,
+        "alu_peaks": alu_peaks,
         "ph_half": ph_half,
         "probing": probe,
         "ldos": ldos_res,
