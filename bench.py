@@ -63,6 +63,8 @@ def parse():
                     help="64x64 fixed-point loop against the L-BFGS driver (field residual vs passes) and exit")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
+    ap.add_argument("--cfg1-study", action="store_true",
+                    help="48x24 cell to self-consistency at 1e-7 (solve.converge) against linear mixing alone, and exit")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
     return ap.parse_args()
@@ -502,7 +504,7 @@ def run_ours(args):
     probe = None if args.no_probing else probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch)
     ldos_res = None if args.no_ldos else ldos_section(kpm, ctx, model, phi, torch.tensor(p0, device="cuda"), torch)
 
-    batched = None if args.no_batched else batched_section(kpm, inputs, torch)
+    batched = None if args.no_batched else batched_section(kpm, inputs, torch, alu)
     adjoint = None if args.no_adjoint else adjoint_section(kpm, inputs, torch)
     precision = precision_section(kpm, inputs, torch)
 
@@ -569,9 +571,12 @@ def run_ours(args):
     return 0
 
 
-def batched_section(kpm, inputs, torch, iters=3):
+def batched_section(kpm, inputs, torch, alu=None, iters=3):
     """32 cells of uneven size and doping (shapes 24x12 .. 64x32), M = 1024,
-    FP32: one batched graph per iteration vs the cells one after another."""
+    FP32: one batched graph per iteration (the persistent recursion: every
+    moment of every cell in one launch, vectors on chip) vs the cells one
+    after another; roofline of the persistent launch against the measured FP32
+    FMA rate (its vectors never leave shared memory)."""
     cells = inputs.cfg3_cells(seed=0, count=32)
     M = 1024
     opts = kpm.make_opts(M, kpm.KPM_FP32)
@@ -589,9 +594,11 @@ def batched_section(kpm, inputs, torch, iters=3):
     kpm.rmft_iterate_batched(ctx, models, opts, ropts, phis, params, mu, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kpm.rmft_iterate_batched(ctx, models, opts, ropts, phis, params, mu, iters)
+    _, bst = kpm.rmft_iterate_batched(ctx, models, opts, ropts, phis, params, mu, iters)
     torch.cuda.synchronize()
     tb = (time.perf_counter() - t0) / iters
+    rec_s = bst[0].recursion_ms / 1e3 / iters
+    row_updates = sum(w.dim * w.dim for w in cells) * (M - 1)
     seq_ctx = [kpm.kpm_create(0) for _ in cells]
     mus = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in cells]
     for k in range(len(cells)):
@@ -607,9 +614,21 @@ def batched_section(kpm, inputs, torch, iters=3):
         kpm.kpm_destroy(c)
     kpm.kpm_destroy(ctx)
     vm = sum(w.dim for w in cells) * M
-    return {"cells": len(cells), "shapes": sorted({f"{w.nx}x{w.ny}" for w in cells}), "M": M, "precision": "fp32",
-            "s_per_iteration": tb, "vector_moments_per_s": vm / tb,
-            "sequential_s_per_iteration": ts, "sequential_vector_moments_per_s": vm / ts, "speedup": ts / tb}
+    out = {"cells": len(cells), "shapes": sorted({f"{w.nx}x{w.ny}" for w in cells}), "M": M, "precision": "fp32",
+           "s_per_iteration": tb, "vector_moments_per_s": vm / tb,
+           "sequential_s_per_iteration": ts, "sequential_vector_moments_per_s": vm / ts, "speedup": ts / tb}
+    if rec_s > 0:
+        # 106 flops per row-column (13 complex multiply-adds, one subtraction)
+        tflops = 106.0 * row_updates / rec_s / 1e12
+        out["persistent_recursion"] = {
+            "s_per_iteration": rec_s, "launches_per_iteration": bst[0].recursion_launches,
+            "effective_gbs": 24.0 * row_updates / rec_s / 1e9,
+            "effective_note": "24 B per row-column (read V_m, V_m-1, write V_m+1) as if streamed; the vectors stay "
+                              "in shared memory",
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": alu[1] if alu else None, "unit": "TFLOP/s",
+                         "frac": tflops / alu[1] if alu else None,
+                         "peak_kind": "measured FP32 FMA rate (kpm_measure_peaks)"}}
+    return out
 
 
 def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
@@ -816,6 +835,41 @@ def lbfgs_study(warm=50, steps_fp=250, iters_lbfgs=40):
     return 0
 
 
+def cfg1_study(linear_budget=6000):
+    """The 48x24 two-vortex cell (M = 1024) to self-consistency at 1e-7:
+    solve.converge (linear FP32 warm-up, Anderson FP32, Anderson with the
+    double-float recursion) against linear FP32 mixing alone for
+    `linear_budget` iterations; iterations, wall time, residual traces."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm, solve
+    build.build()
+    w = inputs.CFG1
+    N = w.n_sites
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    p = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rec = solve.converge(kpm, ctx, model, phi, p, mu, w.n_target, w.M, tol=1e-7)
+    q = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    mq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ro = kpm.make_rmft_opts(w.n_target, tol=1e-7, sync_every=10)
+    lin, done, t0 = [], 0, time.perf_counter()
+    while done < linear_budget:
+        _, st = kpm.rmft_iterate(ctx, model, kpm.make_opts(w.M, kpm.KPM_FP32), ro, phi, q, mq, 250)
+        done += st.iterations
+        lin.append((done, st.residual, st.density_error))
+        if st.converged:
+            break
+    out = {"cell": "48x24", "M": w.M, "delta": w.delta, "tol": 1e-7, "converge": rec,
+           "linear_only": {"iterations": done, "s": time.perf_counter() - t0, "trace": lin,
+                           "residual": lin[-1][1], "converged": bool(st.converged)}}
+    kpm.kpm_destroy(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def profile_adjoint(full=False):
     """Adjoint case for ncu: the 64x64 cell, FP32.  Small (default): M = 64,
     checkpoints every 8 moments, slabs of 2048 columns (134 MB per slab
@@ -909,6 +963,8 @@ def main():
         return profile_probing()
     if args.lbfgs_study:
         return lbfgs_study()
+    if args.cfg1_study:
+        return cfg1_study()
     if args.profile_adjoint:
         return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":

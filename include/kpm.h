@@ -283,15 +283,22 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
 
 /* Batched self-consistency (cells of uneven size, doping and field): up to
  * n_iter iterations of rmft_iterate's loop for ncell independent cells,
- * replayed as one CUDA graph per iteration.  Cells of equal (nx, ny) share
- * one batched recursion launch per Chebyshev step (FP32; FP64 runs the cells
- * of a shape in sequence), and the shape classes run on concurrent streams.
- * models, ropts, phis, params, stats: arrays of ncell entries (host arrays;
- * phis[c] and params[c] device pointers of 4N_c and 26N_c doubles, updated in
- * place); mu_eff: device array of ncell doubles (updated); opts shared (M,
- * precision).  At most 64 cells of one shape in FP32.  Stops early when every
- * cell meets its tol; stats[c] as in rmft_iterate (recursion timing not
- * recorded). */
+ * replayed as one CUDA graph per iteration.  FP32: every cell whose band of
+ * ceil(ny / 8) lattice rows fits shared memory (nx up to 64 at ny = 32) runs
+ * the persistent recursion: one launch per iteration for all of them, in
+ * which a cluster of 8 CTAs holds a 16-column chunk of one cell on chip for
+ * all M moments (work items longest first); cells that do not fit share one
+ * batched step launch per Chebyshev step per shape, on concurrent streams.
+ * FP64 runs the cells of a shape in sequence.  models, ropts, phis, params,
+ * stats: arrays of ncell entries (host arrays; phis[c] and params[c] device
+ * pointers of 4N_c and 26N_c doubles, updated in place); mu_eff: device array
+ * of ncell doubles (updated); opts shared (M, precision; no site range).  At
+ * most 64 cells of one shape in FP32; ropts[c].anderson must be 0 and
+ * sync_every <= 1.  Stops early when every cell meets its tol; stats[c] as in
+ * rmft_iterate, with recursion_ms the device time of the persistent launch
+ * summed over the iterations (the same for every cell; 0 when no cell runs
+ * it), recursion_bytes the cell's streaming-equivalent bytes of those
+ * iterations (24 B per row-column and step) and recursion_launches 1. */
 int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const kpm_opts* opts,
                          const kpm_rmft_opts* ropts, const double* const* phis, double* const* params,
                          double* mu_eff, int n_iter, kpm_rmft_stats* stats, void* stream);

@@ -89,6 +89,13 @@ struct kpm_ctx {
   cudaGraphExec_t bgraph = nullptr;
   std::vector<char> bkey;
   std::vector<void*> bmaps;        // per shape class: device copy of its cells' slab tensor maps
+  // persistent recursion of the batch: cell table, work items (longest first),
+  // item counter; events around its launch
+  void* pbuf = nullptr;
+  size_t pbuf_bytes = 0;
+  cudaEvent_t pev[2] = {nullptr, nullptr};
+  int p_launched = 0;              // 1 when the captured batch graph holds the persistent launch
+  double p_bytes = 0;              // its streaming-equivalent bytes per iteration
 
   // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass, probe_p)
   std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> tuned;
@@ -495,6 +502,9 @@ int kpm_destroy(kpm_ctx* ctx) {
   for (auto& c : ctx->cells)
     if (c.mem) cudaFree(c.mem);
   for (void* p : ctx->bmaps) cudaFree(p);
+  if (ctx->pbuf) cudaFree(ctx->pbuf);
+  for (cudaEvent_t e : ctx->pev)
+    if (e) cudaEventDestroy(e);
   for (cudaStream_t st : ctx->fork) cudaStreamDestroy(st);
   for (cudaEvent_t e : ctx->fork_ev) cudaEventDestroy(e);
   if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
@@ -1059,6 +1069,31 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prepare");
   }
 
+  // FP32 shape classes whose band of a cell fits shared memory run the
+  // persistent recursion (one launch for all of them, all M moments on chip);
+  // the others keep one batched step launch per moment
+  std::vector<char> persist(members.size(), 0);
+  size_t psmem = 0;
+  int pclusters = 0;
+  if (prec == KPM_FP32 && M >= 1) {
+    for (size_t k = 0; k < members.size(); ++k) {
+      const kpm_model& m0 = models[members[k][0]];
+      const size_t sm = persist_smem_bytes(m0.nx, m0.ny);
+      if (sm <= 227 * 1024) {
+        persist[k] = 1;
+        psmem = std::max(psmem, sm);
+      }
+    }
+    if (psmem > 0) {
+      cudaError_t e = persist_prepare(psmem, &pclusters);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::fill(persist.begin(), persist.end(), 0);
+        psmem = 0;
+      }
+    }
+  }
+
   // per-cell scratch, one allocation per cell
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   bool realloc = (int)ctx->cells.size() != ncell;
@@ -1067,8 +1102,9 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
     const int N = models[c].nx * models[c].ny;
     const int64_t D = 2 * (int64_t)N;
     const int k = cls_of[std::make_pair(models[c].nx, models[c].ny)];
+    // (cells of the persistent recursion keep their vectors in shared memory: no slabs)
     need[c] = al(26 * (size_t)N * 8) * 2 + al((size_t)M * 8) * 2 + al(16 * 8) + al((size_t)D * kSlots * 16) +
-              al((size_t)N * table_bytes_per_site(prec)) + 2 * al((size_t)D * plans[k].ldv * elem);
+              al((size_t)N * table_bytes_per_site(prec)) + (persist[k] ? 0 : 2 * al((size_t)D * plans[k].ldv * elem));
     if (!realloc && ctx->cells[c].bytes < need[c]) realloc = true;
   }
   if (realloc) {
@@ -1100,8 +1136,12 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
     C.misc = (double*)b; b += al(16 * 8);
     C.acc = (double2*)b; b += al((size_t)D * kSlots * 16);
     C.table = b; b += al((size_t)N * table_bytes_per_site(prec));
-    C.A = b; b += al((size_t)D * plans[k].ldv * elem);
-    C.B = b;
+    if (persist[k]) {
+      C.A = C.B = nullptr;
+    } else {
+      C.A = b; b += al((size_t)D * plans[k].ldv * elem);
+      C.B = b;
+    }
     C.cls = k;
   }
   if (!ctx->bred && cudaMalloc(&ctx->bred, reduce_scratch_doubles(0) * sizeof(double)) != cudaSuccess) {
@@ -1179,7 +1219,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       }
       KPM_CU(cudaStreamSynchronize(c0));  // no replay of an older graph still reads the maps
       for (size_t k = 0; k < members.size(); ++k) {
-        if (plans[k].tma_rows == 0) continue;
+        if (plans[k].tma_rows == 0 || persist[k]) continue;
         const int nz = (int)members[k].size();
         std::vector<CUtensorMap> host((size_t)2 * nz);
         KPM_CU(encode_batch_maps(plans[k], nz, bps[k], host.data()));
@@ -1187,6 +1227,57 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
         maps_of[k] = ctx->bmaps[k];
       }
     }
+    // persistent recursion: the cell table and the work items, longest first
+    // (an item's time grows with its cell's band, nx ceil(ny / kPClu) sites),
+    // uploaded before the capture like the tensor maps
+    int nitems = 0, nx_max = 0, nclu = 0;
+    PCell* d_cells = nullptr;
+    PItem* d_items = nullptr;
+    int* d_counter = nullptr;
+    void* d_xbuf = nullptr;
+    double pbytes = 0.0;
+    if (psmem > 0) {
+      std::vector<PCell> hc(ncell);
+      std::vector<PItem> hi;
+      const int q = persist_columns();
+      for (int c = 0; c < ncell; ++c) {
+        kpm_ctx::Cell& C = ctx->cells[c];
+        hc[c] = PCell{models[c].nx, models[c].ny, (const float2*)C.table, C.acc, C.am, C.ao};
+        if (!persist[C.cls]) continue;
+        const int64_t D = 2 * (int64_t)models[c].nx * models[c].ny;
+        nx_max = std::max(nx_max, models[c].nx);
+        for (int64_t q0 = 0; q0 < D; q0 += q) hi.push_back(PItem{c, (int)q0});
+        pbytes += 24.0 * (double)D * (double)D * (double)std::max(0, M - 1);
+      }
+      std::stable_sort(hi.begin(), hi.end(), [&](const PItem& a, const PItem& b) {
+        auto cost = [&](const PItem& t) {
+          const kpm_model& m = models[t.cell];
+          return (int64_t)m.nx * ((m.ny + kPClu - 1) / kPClu);
+        };
+        return cost(a) > cost(b);
+      });
+      nitems = (int)hi.size();
+      nclu = std::max(1, std::min(pclusters, nitems));
+      const size_t xoff = al(sizeof(PCell) * ncell) + al(sizeof(PItem) * std::max(1, nitems)) + 256;
+      const size_t need = xoff + persist_exchange_bytes(nclu, nx_max);
+      KPM_CU(cudaStreamSynchronize(c0));  // no replay of an older graph still reads the tables
+      if ((r = ensure(ctx, &ctx->pbuf, &ctx->pbuf_bytes, need))) return r;
+      char* pb = static_cast<char*>(ctx->pbuf);
+      d_cells = reinterpret_cast<PCell*>(pb);
+      d_items = reinterpret_cast<PItem*>(pb + al(sizeof(PCell) * ncell));
+      d_counter = reinterpret_cast<int*>(pb + al(sizeof(PCell) * ncell) + al(sizeof(PItem) * std::max(1, nitems)));
+      d_xbuf = pb + xoff;
+      KPM_CU(cudaMemcpy(d_cells, hc.data(), sizeof(PCell) * ncell, cudaMemcpyHostToDevice));
+      if (nitems) KPM_CU(cudaMemcpy(d_items, hi.data(), sizeof(PItem) * nitems, cudaMemcpyHostToDevice));
+      for (int k = 0; k < 2; ++k)
+        if (!ctx->pev[k] && cudaEventCreate(&ctx->pev[k]) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(ctx, KPM_ECUDA, "event creation failed");
+        }
+    }
+    ctx->p_bytes = pbytes;
+    ctx->p_launched = nitems > 0;
+
     KPM_CU(cudaStreamBeginCapture(c0, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     const char* where = "";
@@ -1210,11 +1301,12 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
         KPM_TRY(launch_scale_table_f32(m, C.fields, C.misc, (float2*)C.table, c0));
       else
         KPM_TRY(launch_scale_table_f64(m, C.fields, C.misc, (double2*)C.table, c0));
-      KPM_TRY(launch_cheb_init(p, prec, C.A, 0, C.acc, C.am, C.ao, c0));
+      if (!persist[C.cls]) KPM_TRY(launch_cheb_init(p, prec, C.A, 0, C.acc, C.am, C.ao, c0));
     }
     // recursion: one chain per shape class on its own stream
     KPM_TRY(cudaEventRecord(ctx->join_ev, c0));
     for (size_t k = 0; k < members.size() && M >= 2; ++k) {
+      if (persist[k]) continue;
       cudaStream_t sk = ctx->fork[k];
       KPM_TRY(cudaStreamWaitEvent(sk, ctx->join_ev, 0));
       const ChebPlan& p = plans[k];
@@ -1236,11 +1328,20 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       KPM_TRY(cudaEventRecord(ctx->fork_ev[k], sk));
       KPM_TRY(cudaStreamWaitEvent(c0, ctx->fork_ev[k], 0));
     }
+    if (nitems > 0) {
+      // every moment of every persistent cell in one launch, concurrent with
+      // the per-step launches of the other shape classes
+      KPM_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), c0));
+      KPM_TRY(cudaEventRecordWithFlags(ctx->pev[0], c0, cudaEventRecordExternal));
+      KPM_TRY(launch_cheb_persist(d_cells, d_items, nitems, d_counter, M, nclu, psmem, d_xbuf, nx_max, c0));
+      KPM_TRY(cudaEventRecordWithFlags(ctx->pev[1], c0, cudaEventRecordExternal));
+    }
     for (int c = 0; c < ncell; ++c) {
       kpm_ctx::Cell& C = ctx->cells[c];
       const int N = models[c].nx * models[c].ny;
       const ChebPlan& p = plans[C.cls];
-      if (M >= 2) KPM_TRY(launch_cheb_gather(p, prec, ((M - 1) & 1) ? C.B : C.A, 0, C.acc, C.am, C.ao, M - 1, c0));
+      if (M >= 2 && !persist[C.cls])
+        KPM_TRY(launch_cheb_gather(p, prec, ((M - 1) & 1) ? C.B : C.A, 0, C.acc, C.am, C.ao, M - 1, c0));
       KPM_TRY(launch_assemble(models[c].nx, models[c].ny, C.acc, C.misc, C.obs, C.misc + 3, ctx->bred, c0));
       KPM_TRY(launch_update(N, params[c], C.obs, mu_eff + c, ropts[c], C.misc + 4, ctx->bred, c0));
       KPM_TRY(cudaMemcpyAsync(ctx->bhost + 16 * c, C.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c0));
@@ -1266,9 +1367,15 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
   std::vector<kpm_rmft_stats> st(ncell);
   memset(st.data(), 0, sizeof(kpm_rmft_stats) * ncell);
   int status = KPM_OK;
+  double pms = 0.0;
   for (int it = 0; it < n_iter; ++it) {
     KPM_CU(cudaGraphLaunch(ctx->bgraph, s));
     KPM_CU(cudaStreamSynchronize(s));
+    if (ctx->p_launched) {
+      float ms = 0.f;
+      KPM_CU(cudaEventElapsedTime(&ms, ctx->pev[0], ctx->pev[1]));
+      pms += ms;
+    }
     bool all = true;
     for (int c = 0; c < ncell; ++c) {
       const double* h = ctx->bhost + 16 * c;
@@ -1288,6 +1395,13 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
       all = all && q.converged;
     }
     if (status != KPM_OK || all) break;
+  }
+  // the persistent launch serves every cell: its time and streaming-equivalent
+  // bytes are reported on each cell of the batch
+  for (auto& q : st) {
+    q.recursion_ms = pms;
+    q.recursion_bytes = ctx->p_launched ? ctx->p_bytes * (double)(q.iterations) : 0.0;
+    q.recursion_launches = ctx->p_launched ? 1 : 0;
   }
   if (stats) memcpy(stats, st.data(), sizeof(kpm_rmft_stats) * ncell);
   return status;

@@ -158,6 +158,32 @@ cudaError_t launch_cheb_gather(const ChebPlan& p, int precision, const void* V, 
                                double2* acc, const double* am, const double* ao, int m,
                                cudaStream_t s);
 
+// persistent batched FP32 recursion: clusters of kPClu CTAs, one item = one
+// chunk of persist_columns() unit columns of one cell for all M moments
+// (moment sums written to cell.acc, including the a_0 terms and the last moment)
+constexpr int kPClu = 8;
+struct PCell {
+  int nx, ny;
+  const float2* table;  // the cell's 2h~ table (FP32)
+  double2* acc;         // its moment sums [D][kSlots]
+  const double* am;
+  const double* ao;
+};
+struct PItem {
+  int cell;  // index into the cell array
+  int q0;    // first unit column of the chunk
+};
+size_t persist_smem_bytes(int nx, int ny);
+int persist_columns();
+// sets the kernel's shared-memory limit; *max_clusters = co-resident clusters at `smem`
+cudaError_t persist_prepare(size_t smem, int* max_clusters);
+// device bytes of the boundary-row exchange buffer of nclusters clusters
+size_t persist_exchange_bytes(int nclusters, int nx_max);
+// items are taken from *counter (zero before the launch) in list order; xbuf:
+// persist_exchange_bytes(nclusters, nx_max) device bytes, nx_max >= every cell's nx
+cudaError_t launch_cheb_persist(const PCell* cells, const PItem* items, int nitems, int* counter, int M, int nclusters,
+                                size_t smem, void* xbuf, int nx_max, cudaStream_t s);
+
 // ---------------------------------------------------------------- kpm_adjoint.cu
 // seed weights w[J][10] of every unit column from the upstream gradients (zero
 // for the columns of sites outside [sb, se), se < 0: N)

@@ -81,3 +81,32 @@ def test_cfg1_one_iteration_residual(K):
     assert st.omega == pytest.approx(omega, rel=1e-11)
     assert np.max(np.abs(p.cpu().numpy() - p1)) < 1e-10
     assert float(mu.item()) == pytest.approx(mu1, abs=1e-10)
+
+
+def test_cfg1_converges_to_1e7(K):
+    """The 48 x 24 two-vortex cell at M = 1024 run to self-consistency at
+    tol = 1e-7 (max parameter change and density error), through
+    solve.converge: 500 linear FP32 iterations, Anderson mixing (reading R4)
+    in FP32 to 1e-6, then Anderson with the double-float recursion.  Reading
+    R3: the oracle's residual at the GPU's final parameters (one FP64 spectral
+    KPM pass and the update of readings R1/R2) is below tol as well."""
+    kpm, ctx = K
+    from paper_2212_05685_gb300 import solve
+    w = inputs.CFG1
+    N = w.n_sites
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    p = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rec = solve.converge(kpm, ctx, model, phi, p, mu, w.n_target, w.M, tol=1e-7)
+    print({k: v for k, v in rec.items() if k != "phases"},
+          [(ph["phase"], ph["iterations"], round(ph["s"], 1), ph["residual"]) for ph in rec["phases"]])
+    assert rec["converged"] and rec["residual"] < 1e-7 and abs(rec["density_error"]) < 1e-7
+    om = rmft.Model(w.nx, w.ny)
+    pf, mf = p.cpu().numpy(), float(mu.item())
+    f, _ = rmft.shifted_fields(om, pf, mf)
+    a, b = bdg.gershgorin(om, f)
+    F1, _ = okpm.f_spectral(bdg.dense(om, f), a, b, w.M)
+    _, _, r, e = rmft.update(pf, okpm.observables(om, F1), w.n_target, mf)
+    assert r < 1e-7 + 1e-9 and abs(e) < 1e-7 + 1e-9
