@@ -781,9 +781,35 @@ def adjoint_section(kpm, inputs, torch):
         torch.cuda.synchronize()
         ts = e[1].elapsed_time(e[2]) / 1e3
         store_all = {"ckpt_every": M, "scratch_budget_gib": 160, "backward_s": ts, "backward_over_forward": ts / tf}
+    # regenerating backward pass (the recursion run backwards from the last two
+    # vectors): after a forward pass that keeps them (the autograd path), and
+    # with its own forward sweep; default scratch budget
+    kpm.kpm_set_scratch_budget(ctx, 24 * 2 ** 30)
+    kept = kpm.make_opts(M, kpm.KPM_FP32, flags=kpm.KPM_FLAG_KEEP_TAIL)
+    kpm.kpm_observables(ctx, model, kept, fields, ab, obs)
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 1.0, out, ckpt_every=kpm.KPM_REGENERATE)
+    torch.cuda.synchronize()
+    e[0].record()
+    kpm.kpm_observables(ctx, model, kept, fields, ab, obs)
+    e[1].record()
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 1.0, out, ckpt_every=kpm.KPM_REGENERATE)
+    e[2].record()
+    torch.cuda.synchronize()
+    tfk, tbr = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    kpm.kpm_observables(ctx, model, opts, fields, ab, obs)  # drops the tail
+    torch.cuda.synchronize()
+    e[1].record()
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 1.0, out, ckpt_every=kpm.KPM_REGENERATE)
+    e[2].record()
+    torch.cuda.synchronize()
+    tbs = e[1].elapsed_time(e[2]) / 1e3
+    regenerate = {"forward_keep_tail_s": tfk, "backward_s": tbr, "backward_over_forward": tbr / tf,
+                  "backward_with_own_sweep_s": tbs, "backward_with_own_sweep_over_forward": tbs / tf,
+                  "note": "alpha_m regenerated by the recursion run backwards from the forward pass's last two "
+                          "vectors (no checkpoints, 4 slab vectors of scratch)"}
     kpm.kpm_destroy(ctx)
     return {"cell": "64x64", "M": M, "ckpt_every": 32, "precision": "fp32", "forward_s": tf, "backward_s": tb,
-            "backward_over_forward": tb / tf, "store_all": store_all}
+            "backward_over_forward": tb / tf, "store_all": store_all, "regenerate": regenerate}
 
 
 def lbfgs_study(warm=50, steps_fp=250, iters_lbfgs=40):

@@ -121,6 +121,17 @@ typedef struct {
  * rescales with b = 0 exactly.  Not accepted by kpm_backward,
  * rmft_iterate_batched and kpm_observables_noalloc (KPM_EINVAL). */
 #define KPM_FLAG_PH_HALF 2
+/* kpm_opts.flags: kpm_observables keeps the last two recursion vectors of every
+ * slab (alpha_{M-2}, alpha_{M-1}; 2 slab vectors per slab of context memory)
+ * and a copy of its fields and ab, so that a following kpm_backward with
+ * ckpt_every = KPM_REGENERATE on the same fields runs no forward sweep.  FP32
+ * or FP64 unit-vector passes (KPM_EINVAL with probing, the half pass or
+ * KPM_DF64); any kpm_observables call without the flag drops the tail. */
+#define KPM_FLAG_KEEP_TAIL 4
+
+/* kpm_backward ckpt_every: regenerate the forward vectors backwards instead
+ * of checkpointing them (see kpm_backward) */
+#define KPM_REGENERATE (-1)
 
 /* Self-consistency options (the paper's iteration, readings R1/R2). */
 typedef struct {
@@ -311,10 +322,21 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
  * through the fields' dependence on the Peierls phases at order parameters
  * `params` (then phi and params are required).  The rescaling ab is held
  * fixed.  Backward recursion lambda_m = c_m + 2 h~ lambda_{m+1} -
- * lambda_{m+2} over all D unit columns, with the forward vectors
- * checkpointed every ckpt_every moments (0 = round(sqrt(M))) and recomputed
- * per segment; stencil-entry sums in FP64.  Scratch: (2 ceil((M-1)/s) + s + 2)
- * slab vectors within the context budget.  All pointers device. */
+ * lambda_{m+2} over all D unit columns (or those of the site range), with
+ * the forward vectors alpha_m either
+ *   ckpt_every >= 0: checkpointed every ckpt_every moments (0 = round(sqrt(M)))
+ *     and recomputed per segment; scratch (2 ceil((M-1)/s) + s + 2) slab
+ *     vectors within the context budget; or
+ *   ckpt_every = KPM_REGENERATE: regenerated in descending m by the same
+ *     recursion run backwards, alpha_{m-1} = 2 h~ alpha_m - alpha_{m+1}, from
+ *     the last two vectors; these come from a forward sweep, or without one
+ *     from the tail the last kpm_observables with KPM_FLAG_KEEP_TAIL left
+ *     when its model, pass options, fields and ab equal this call's (checked
+ *     on the device; one stream synchronisation); scratch 4 slab vectors.
+ *     The recursion's rounding in reverse is bounded like its forward
+ *     rounding (both run the neutrally stable three-term recurrence on
+ *     eigenvalues in [-1, 1]).
+ * Stencil-entry sums in FP64.  All pointers device. */
 int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
                  const double* ab, const double* grad_obs, double grad_omega, double* grad_fields,
                  const double* phi, const double* params, double* grad_phi, int ckpt_every, void* stream);

@@ -4,6 +4,12 @@ forward:  fields (26*N float64, CUDA) -> (obs 26*N, omega 1) via kpm_observables
 backward: (dL/dobs, dL/domega) -> dL/dfields via kpm_backward (App. B backward
           recursion, rescaling held fixed)
 
+By default (ckpt_every = KPM_REGENERATE) the forward pass keeps the last two
+recursion vectors of every slab (KPM_FLAG_KEEP_TAIL) and the backward pass
+regenerates the earlier ones by running the recursion backwards, so it needs
+no checkpoints and no forward sweep of its own; ckpt_every >= 0 selects the
+checkpointing backward pass instead.
+
 Real-valued torch tensors in the library's layouts; complex entries are
 stored as (re, im) pairs, so torch's real gradients are exactly the
 (dL/dRe, dL/dIm) convention of the C ABI.
@@ -21,7 +27,10 @@ class KPMObservables(torch.autograd.Function):
         N = model.nx * model.ny
         obs = torch.empty(26 * N, dtype=torch.float64, device=fields.device)
         omega = torch.empty(1, dtype=torch.float64, device=fields.device)
-        kpm.kpm_observables(kctx, model, opts, fields.detach().contiguous(), ab, obs, omega)
+        fo = kpm.kpm_opts.from_buffer_copy(opts)
+        if ckpt_every == kpm.KPM_REGENERATE:
+            fo.flags |= kpm.KPM_FLAG_KEEP_TAIL
+        kpm.kpm_observables(kctx, model, fo, fields.detach().contiguous(), ab, obs, omega)
         ctx.save_for_backward(fields, ab)
         ctx.kctx, ctx.model, ctx.opts, ctx.ckpt = kctx, model, opts, ckpt_every
         return obs, omega
@@ -39,7 +48,7 @@ class KPMObservables(torch.autograd.Function):
         return grad, None, None, None, None, None
 
 
-def observables(kctx, model, opts, fields, ab, ckpt_every=0):
+def observables(kctx, model, opts, fields, ab, ckpt_every=kpm.KPM_REGENERATE):
     """Differentiable KPM observables and grand potential of the Nambu matrix
     built from `fields` (ab = spectral rescale, not differentiated)."""
     return KPMObservables.apply(fields, ab, kctx, model, opts, ckpt_every)

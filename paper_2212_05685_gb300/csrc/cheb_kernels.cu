@@ -564,10 +564,7 @@ __device__ __forceinline__ void moment_sums(const float4* wm, const float4* w0, 
     const float4* w = dy < 0 ? wm : (dy > 0 ? wp : w0);
     const int al = kSlotFlip[s] ? 1 - beta : beta;
     const float2 val = pair_elem(w + xsl * RS + nambu_slot<NV, SW>(xsl, al) * NV, c);
-    if (cmap.probe_p)
-      acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
-    else
-      acc_add_unit(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, (double)val.x, (double)val.y);
+    acc_add(acc + J * kSlots + s, s == kSlots - 1 ? co : cm, wgt, (double)val.x, (double)val.y);
     if (s == 0 && cmap.rec) record_diag(cmap, D, m, J, wgt, (double)val.x, (double)val.y);
   }
 }

@@ -392,7 +392,29 @@ __global__ void grad_fields_kernel(int nx, int ny, const double2* __restrict__ G
   }
 }
 
+// out = 1 when a[0..n) equals b[0..n) and c[0..k) equals d[0..k) bit for bit
+__global__ void differ_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                              const double* __restrict__ c, const double* __restrict__ d, int k,
+                              int* __restrict__ differ) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + k; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = i < n ? a[i] : c[i - n], y = i < n ? b[i] : d[i - n];
+    if (__double_as_longlong(x) != __double_as_longlong(y)) atomicOr(differ, 1);
+  }
+}
 }  // namespace
+
+cudaError_t launch_same_doubles(const double* a, const double* b, int64_t n, const double* c, const double* d, int k,
+                                int* flag, int* host, int* same, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + k + 255) / 256, 4 * kSMs));
+  differ_kernel<<<grid, 256, 0, s>>>(a, b, n, c, d, k, flag);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(host, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  *same = *host == 0;
+  return cudaSuccess;
+}
 
 cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const double* ab, double g_omega,
                                 double2* w, cudaStream_t s, int sb, int se) {

@@ -55,6 +55,17 @@ struct kpm_ctx {
   size_t and_bytes = 0;
   double* peak_buf = nullptr;   // scratch of kpm_measure_peaks
   size_t peak_bytes = 0;
+  // tail of the last kpm_observables with KPM_FLAG_KEEP_TAIL: per slab the last
+  // two recursion vectors (alpha_{M-2}, alpha_{M-1}); the fields and ab it ran
+  // on (26 N + 2 doubles) and the pass it belongs to
+  void* tail = nullptr;
+  size_t tail_bytes = 0;
+  double* tail_in = nullptr;
+  size_t tail_in_bytes = 0;
+  bool tail_valid = false;
+  kpm_model tail_model;
+  kpm_opts tail_opts;
+  int64_t tail_width = 0, tail_c0 = 0, tail_c1 = 0;
   // adjoint scratch: checkpoints, segment, lambda buffers; stencil gradient; seed weights
   void* bwd = nullptr;
   size_t bwd_bytes = 0;
@@ -326,7 +337,7 @@ int ensure_pass_scratch(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, con
 int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const PassPlan& pp, const double* fields,
                  const double* ab, double* obs, double* omega, cudaStream_t s, bool events = false,
                  int* launches = nullptr, int* rec_launches = nullptr, double* rec_bytes = nullptr,
-                 double* diag_record = nullptr) {
+                 double* diag_record = nullptr, void* tail = nullptr) {
   ChebPlan p = pp.cheb;
   p.rec = diag_record;
   int nl0 = 0;
@@ -383,6 +394,11 @@ int enqueue_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, const Pass
     if (M >= 2) {
       KPM_CU(launch_cheb_gather(p, prec, X1, s0, ctx->acc, ctx->am, ctx->ao, M - 1, s));
       nl += 1;
+      if (tail) {  // alpha_{M-2}, alpha_{M-1} of this slab for a later backward pass
+        char* t = static_cast<char*>(tail) + (size_t)(2 * ((s0 - pp.c0) / pp.width)) * (size_t)vec;
+        KPM_CU(cudaMemcpyAsync(t, X0, (size_t)vec, cudaMemcpyDeviceToDevice, s));
+        KPM_CU(cudaMemcpyAsync(t + (size_t)vec, X1, (size_t)vec, cudaMemcpyDeviceToDevice, s));
+      }
     }
   }
   KPM_CU(launch_assemble(m->nx, m->ny, ctx->acc, ab, obs, omega, ctx->red, s, p.js, pp.sb, pp.se));
@@ -492,7 +508,7 @@ int kpm_destroy(kpm_ctx* ctx) {
   drop_graph(ctx);
   cublas_destroy(ctx->cublas);
   for (void* p : {ctx->slab[0], ctx->slab[1], ctx->slab[2], ctx->slab[3], (void*)ctx->xi, (void*)ctx->ldos_buf,
-                  (void*)ctx->and_buf, (void*)ctx->peak_buf,
+                  (void*)ctx->and_buf, (void*)ctx->peak_buf, ctx->tail, (void*)ctx->tail_in,
                   (void*)ctx->acc, ctx->table, (void*)ctx->am, (void*)ctx->ao,
                   (void*)ctx->red, (void*)ctx->fields, (void*)ctx->obs, (void*)ctx->wsite, (void*)ctx->dparams,
                   (void*)ctx->dphi, (void*)ctx->misc, ctx->bwd, (void*)ctx->Gacc, (void*)ctx->wseed})
@@ -631,7 +647,32 @@ int kpm_observables(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, 
   if (opts->flags & KPM_FLAG_PH_HALF) {
     if ((r = check_ph_sector(ctx, model, fields, ab, (cudaStream_t)stream))) return r;
   }
-  return enqueue_pass(ctx, model, opts, pp, fields, ab, obs, omega, (cudaStream_t)stream);
+  void* tail = nullptr;
+  ctx->tail_valid = false;
+  if ((opts->flags & KPM_FLAG_KEEP_TAIL) && opts->M >= 2) {
+    if (opts->precision == KPM_DF64 || opts->probe_p || (opts->flags & KPM_FLAG_PH_HALF))
+      return fail(ctx, KPM_EINVAL, "KPM_FLAG_KEEP_TAIL: FP32 or FP64 unit-vector passes only");
+    const int N = model->nx * model->ny;
+    const size_t vec = (size_t)pp.cheb.D * pp.cheb.ldv * pp.elem;
+    const int64_t nslab = (pp.c1 - pp.c0 + pp.width - 1) / pp.width;
+    if ((r = ensure(ctx, &ctx->tail, &ctx->tail_bytes, 2 * (size_t)nslab * vec))) return r;
+    if ((r = ensure(ctx, &ctx->tail_in, &ctx->tail_in_bytes, (26 * (size_t)N + 2) * sizeof(double)))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    KPM_CU(cudaMemcpyAsync(ctx->tail_in, fields, 26 * (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KPM_CU(cudaMemcpyAsync(ctx->tail_in + 26 * (size_t)N, ab, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    tail = ctx->tail;
+  }
+  r = enqueue_pass(ctx, model, opts, pp, fields, ab, obs, omega, (cudaStream_t)stream, false, nullptr, nullptr,
+                   nullptr, nullptr, tail);
+  if (r == KPM_OK && tail) {
+    ctx->tail_valid = true;
+    ctx->tail_model = *model;
+    ctx->tail_opts = *opts;
+    ctx->tail_width = pp.width;
+    ctx->tail_c0 = pp.c0;
+    ctx->tail_c1 = pp.c1;
+  }
+  return r;
 }
 
 int check_rmft_opts(kpm_ctx* ctx, const kpm_rmft_opts* ro) {
@@ -843,15 +884,19 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
                    (r = check_dev(ctx, params, "params"))))
     return r;
   if (!opts) return fail(ctx, KPM_EINVAL, "opts is null");
-  if (ckpt_every < 0) return fail(ctx, KPM_EINVAL, "ckpt_every must be >= 0");
+  if (ckpt_every < KPM_REGENERATE) return fail(ctx, KPM_EINVAL, "ckpt_every must be >= 0 or KPM_REGENERATE");
   DeviceGuard g(ctx->device);
   const int N = model->nx * model->ny;
   const int64_t D = 2 * (int64_t)N;
   const int M = opts->M;
+  const bool regen = ckpt_every == KPM_REGENERATE;
   int seg = ckpt_every > 0 ? ckpt_every : (int)lround(sqrt((double)M));
   if (seg < 2) seg = 2;
-  const int K = M >= 2 ? (M - 1 + seg - 1) / seg : 0;  // segments, each serving m in [k seg + 1, (k+1) seg]
-  const int nvec = 2 * K + seg + 2;                    // checkpoints, segment, lambda pair
+  // checkpoints: segments serving m in [k seg + 1, (k+1) seg], each with two
+  // checkpoints; regenerating: no checkpoints, only the lambda pair here (the
+  // alpha pair lives in the recursion slabs)
+  const int K = regen ? 0 : (M >= 2 ? (M - 1 + seg - 1) / seg : 0);
+  const int nvec = regen ? 2 : 2 * K + seg + 2;
 
   if (opts->precision == KPM_DF64) return fail(ctx, KPM_EINVAL, "KPM_DF64: not supported by kpm_backward");
   if (opts && (opts->flags & KPM_FLAG_PH_HALF)) return fail(ctx, KPM_EINVAL, "KPM_FLAG_PH_HALF: not supported by kpm_backward");
@@ -859,8 +904,27 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   // slab width from the budget over all adjoint slab vectors (plus the forward pair);
   // the adjoint steps one moment per launch (its recomputed segments are stored)
   kpm_opts o = *opts;
-  o.flags &= ~KPM_FLAG_DOUBLE_STEP;
+  o.flags &= ~(KPM_FLAG_DOUBLE_STEP | KPM_FLAG_KEEP_TAIL);
   const size_t elem = o.precision == KPM_FP32 ? 8 : 16;
+  // regenerating from the tail of the last kpm_observables: same model, same
+  // pass options and the same fields and ab (compared on the device below)
+  bool use_tail = false;
+  if (regen && ctx->tail_valid && M >= 2) {
+    kpm_opts t = ctx->tail_opts;
+    t.flags &= ~(KPM_FLAG_DOUBLE_STEP | KPM_FLAG_KEEP_TAIL);
+    kpm_opts q = o;
+    if (q.block_width == 0) q.block_width = t.block_width;
+    use_tail = memcmp(&ctx->tail_model, model, sizeof(kpm_model)) == 0 && memcmp(&t, &q, sizeof(kpm_opts)) == 0;
+    if (use_tail) {
+      int same = 0;
+      if ((r = ensure_misc(ctx))) return r;
+      KPM_CU(launch_same_doubles(fields, ctx->tail_in, 26 * (int64_t)N, ab, ctx->tail_in + 26 * (size_t)N, 2,
+                                 reinterpret_cast<int*>(ctx->misc + 14), reinterpret_cast<int*>(ctx->host_misc + 14),
+                                 &same, (cudaStream_t)stream));
+      use_tail = same != 0;
+    }
+    if (use_tail) o.block_width = (int)ctx->tail_width;  // the forward's slabs
+  }
   // unit columns of the pass (all D, or those of the site range)
   const int64_t ncol = (o.site_begin != 0 || o.site_end != 0) ? 2 * ((int64_t)o.site_end - o.site_begin) : D;
   if (o.block_width == 0 && ncol > 0) {
@@ -900,7 +964,48 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const double* am = ctx->am;
   const double* ao = ctx->ao;
 
-  for (int64_t s0 = pp.c0; s0 < pp.c1 && M >= 2; s0 += pp.width) {
+  // Reversible recursion: alpha_{m-1} = 2 h~ alpha_m - alpha_{m+1} (Eq. alpha
+  // run backwards), so from the last two vectors every earlier one is
+  // regenerated by one more step, in the order the backward sweep needs them.
+  for (int64_t s0 = pp.c0; regen && s0 < pp.c1 && M >= 2; s0 += pp.width) {
+    void* hi = A;  // alpha_{M-1}
+    void* lo = B;  // alpha_{M-2}
+    if (use_tail) {
+      const char* t = static_cast<const char*>(ctx->tail) + (size_t)(2 * ((s0 - pp.c0) / pp.width)) * vbytes;
+      KPM_CU(cudaMemcpyAsync(lo, t, vbytes, cudaMemcpyDeviceToDevice, s));
+      KPM_CU(cudaMemcpyAsync(hi, t + vbytes, vbytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+      // forward sweep keeping only the last pair: X0 = alpha_{mm-1}, X1 = alpha_mm
+      void* X0 = A;
+      void* X1 = B;
+      KPM_CU(launch_cheb_init(p, prec, X0, s0, ctx->acc, am, ao, s));
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, X0, X1, s0, nullptr, am, ao, 0, 0, s));
+      for (int mm = 1; mm + 1 <= M - 1; ++mm) {
+        KPM_CU(launch_cheb_step(p, prec, ctx->table, X1, X0, s0, nullptr, am, ao, mm, 1, s));
+        std::swap(X0, X1);
+      }
+      hi = X1;
+      lo = X0;
+    }
+    void* lcur = lamA;
+    void* lnxt = lamB;
+    KPM_CU(cudaMemsetAsync(lcur, 0, vbytes, s));
+    KPM_CU(cudaMemsetAsync(lnxt, 0, vbytes, s));
+    for (int m = M - 1; m >= 1; --m) {
+      if (m < M - 1) {
+        // alpha_{m-1} = 2 h~ alpha_m - alpha_{m+1}, in place over alpha_{m+1}
+        KPM_CU(launch_cheb_step(p, prec, ctx->table, lo, hi, s0, nullptr, am, ao, 0, 1, s));
+        std::swap(hi, lo);
+      }
+      // lnxt <- 2 h~ lambda_{m+1} - lambda_{m+2} + c_m = lambda_m
+      KPM_CU(launch_cheb_step(p, prec, ctx->table, lcur, lnxt, s0, nullptr, am, ao, 0, 1, s));
+      KPM_CU(launch_seed_scatter(p, prec, lnxt, s0, ctx->wseed, am, ao, m, s));
+      KPM_CU(launch_grad_accum(p, prec, lnxt, lo, m == 1 ? 1.0 : 2.0, Gpart, s));
+      std::swap(lcur, lnxt);
+    }
+  }
+
+  for (int64_t s0 = pp.c0; !regen && s0 < pp.c1 && M >= 2; s0 += pp.width) {
     // forward, writing the checkpointed vectors (alpha_{k seg}, alpha_{k seg + 1})
     // in place and stepping through the two temporaries otherwise
     auto ckpt_slot = [&](int idx) -> void* {

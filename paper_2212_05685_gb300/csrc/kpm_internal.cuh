@@ -185,6 +185,10 @@ cudaError_t launch_cheb_persist(const PCell* cells, const PItem* items, int nite
                                 size_t smem, void* xbuf, int nx_max, cudaStream_t s);
 
 // ---------------------------------------------------------------- kpm_adjoint.cu
+// *same = 1 when a = b (n doubles) and c = d (k doubles) bit for bit; flag: a
+// device int, host: a pinned host int; synchronises s
+cudaError_t launch_same_doubles(const double* a, const double* b, int64_t n, const double* c, const double* d, int k,
+                                int* flag, int* host, int* same, cudaStream_t s);
 // seed weights w[J][10] of every unit column from the upstream gradients (zero
 // for the columns of sites outside [sb, se), se < 0: N)
 cudaError_t launch_seed_weights(int nx, int ny, const double* grad_obs, const double* ab, double g_omega,

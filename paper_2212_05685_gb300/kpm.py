@@ -26,6 +26,8 @@ KPM_FP32 = 1
 KPM_DF64 = 2
 KPM_FLAG_DOUBLE_STEP = 1
 KPM_FLAG_PH_HALF = 2
+KPM_FLAG_KEEP_TAIL = 4
+KPM_REGENERATE = -1
 
 
 class kpm_model(ctypes.Structure):

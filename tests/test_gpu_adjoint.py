@@ -201,3 +201,74 @@ def test_backward_is_deterministic(K, prec):
     a, _ = _gpu_grad(K, model, fields, ab, M, p, g, 0.7, bw=64, ckpt=7)
     b, _ = _gpu_grad(K, model, fields, ab, M, p, g, 0.7, bw=64, ckpt=7)
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- regenerating backward sweep
+@pytest.mark.parametrize("nx,ny,M,bw,prec", [(4, 4, 24, 0, 0), (7, 4, 64, 13, 0), (12, 8, 128, 0, 1),
+                                              (18, 10, 96, 40, 1)])
+def test_regenerate_matches_oracle(K, nx, ny, M, bw, prec):
+    """ckpt_every = KPM_REGENERATE (alpha_m rebuilt by the recursion run
+    backwards from its last two vectors, Eq. alpha): the oracle's
+    Daleckii-Krein gradient to 1e-10 (FP64) and 2e-5 relative (FP32)."""
+    kpm, _ = K
+    w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), M)
+    p = inputs.vortex_seed(w) if prec == 1 else inputs.random_params(nx, ny, 3)
+    model, phi, params, fields, ab = _prep(K, nx, ny, p)
+    rng = np.random.default_rng(nx + ny)
+    g_obs, g_om = rng.normal(size=26 * nx * ny), 0.4
+    got, _ = _gpu_grad(K, model, fields, ab, M, prec, g_obs, g_om, bw=bw, ckpt=kpm.KPM_REGENERATE)
+    ref = adjoint.vjp_dense(rmft.Model(nx, ny), fields.cpu().numpy(), *ab.cpu().numpy(), M, g_obs, g_om)
+    tol = 1e-10 if prec == 0 else 2e-5
+    assert np.max(np.abs(got - ref)) < tol * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_regenerate_from_kept_tail(K, prec):
+    """A kpm_observables with KPM_FLAG_KEEP_TAIL leaves the last two vectors
+    of every slab; the regenerating backward pass on the same fields then runs
+    no forward sweep and gives the same bits as with its own sweep; after the
+    fields change the tail is not used (the gradient follows the new fields)."""
+    kpm, ctx = K
+    nx, ny, M = 10, 8, 80
+    N = nx * ny
+    w = inputs.Workload(nx, ny, 0.15, inputs.two_vortex(nx, ny), M, seed=2)
+    model, phi, params, fields, ab = _prep(K, nx, ny, inputs.vortex_seed(w))
+    g = dev(np.random.default_rng(4).normal(size=26 * N))
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    opts = kpm.make_opts(M, prec, 48)
+    kpm.kpm_observables(ctx, model, opts, fields, ab, obs)  # no tail
+    own = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 0.3, own, ckpt_every=kpm.KPM_REGENERATE)
+    kept = kpm.make_opts(M, prec, 48, flags=kpm.KPM_FLAG_KEEP_TAIL)
+    obs2 = torch.empty_like(obs)
+    kpm.kpm_observables(ctx, model, kept, fields, ab, obs2)
+    assert torch.equal(obs, obs2)
+    tail = torch.empty_like(own)
+    kpm.kpm_backward(ctx, model, opts, fields, ab, g, 0.3, tail, ckpt_every=kpm.KPM_REGENERATE)
+    assert torch.equal(own, tail)
+    # changed fields after the forward pass: the tail no longer matches
+    fields2 = fields.clone()
+    fields2[:N] += 0.01
+    new = torch.empty_like(own)
+    kpm.kpm_backward(ctx, model, opts, fields2, ab, g, 0.3, new, ckpt_every=kpm.KPM_REGENERATE)
+    ref = adjoint.vjp_dense(rmft.Model(nx, ny), fields2.cpu().numpy(), *ab.cpu().numpy(), M, g.cpu().numpy(), 0.3)
+    tol = 1e-10 if prec == 0 else 2e-5
+    assert np.max(np.abs(new.cpu().numpy() - ref)) < tol * max(1.0, np.max(np.abs(ref)))
+
+
+def test_autograd_regenerates_from_forward_tail(K):
+    """The autograd Function keeps the forward pass's tail and regenerates:
+    its gradient equals kpm_backward with checkpoints (FP64, 1e-12)."""
+    kpm, ctx = K
+    from paper_2212_05685_gb300 import autograd
+    nx, ny, M = 8, 6, 64
+    N = nx * ny
+    model, phi, params, fields, ab = _prep(K, nx, ny, inputs.random_params(nx, ny, 8))
+    opts = kpm.make_opts(M, kpm.KPM_FP64)
+    f = fields.clone().requires_grad_(True)
+    obs, om = autograd.observables(ctx, model, opts, f, ab)
+    wgt = dev(np.random.default_rng(6).normal(size=26 * N))
+    ((obs * wgt).sum() + 0.2 * om.sum()).backward()
+    ref = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_backward(ctx, model, opts, fields, ab, wgt, 0.2, ref, ckpt_every=8)
+    assert float((f.grad - ref).abs().max()) < 1e-12 * max(1.0, float(ref.abs().max()))
