@@ -65,6 +65,8 @@ def parse():
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
     ap.add_argument("--cfg1-study", action="store_true",
                     help="48x24 cell to self-consistency at 1e-7 (solve.converge) against linear mixing alone, and exit")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="one batched iteration (4 cells 48x24 and 2 cells 64x32, M=64, FP32) for ncu captures")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
     return ap.parse_args()
@@ -390,7 +392,7 @@ def run_ours(args):
     # measured FMA rates of the FP64 and FP32 pipes (the ALU-bound rooflines)
     alu = kpm.kpm_measure_peaks(ctx)
     alu_peaks = {"fp64_tflops": alu[0], "fp32_tflops": alu[1], "fp32x2_tflops": alu[2], "sm_mhz": alu[3],
-                 "how": "independent FMA chains (8 per thread, 4 x 256 threads per SM), best of 3 launches, "
+                 "how": "independent FMA chains (8 per thread, 4 x 256 threads per SM), best of 3 launches for each of two operand patterns (shared or per-chain multiplier and addend), "
                         "CUDA events (kpm_measure_peaks)"}
     props = torch.cuda.get_device_properties(0)
     sm_count = props.multi_processor_count
@@ -954,6 +956,33 @@ def profile_probing():
     return 0
 
 
+def profile_batched():
+    """Small batch for ncu: 4 cells of 48x24 and 2 of 64x32, M = 64, FP32,
+    one iteration of the batched call (one persistent recursion launch)."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    ctx = kpm.kpm_create(0)
+    shapes = [(48, 24)] * 4 + [(64, 32)] * 2
+    models, phis, params, ropts = [], [], [], []
+    for k, (nx, ny) in enumerate(shapes):
+        w = inputs.Workload(nx, ny, 0.15, inputs.two_vortex(nx, ny), 64, seed=k)
+        m = kpm.make_model(nx, ny)
+        phi = torch.empty(4 * w.n_sites, dtype=torch.float64, device="cuda")
+        kpm.kpm_peierls_phases(ctx, m, phi)
+        models.append(m)
+        phis.append(phi)
+        params.append(torch.tensor(inputs.vortex_seed(w), device="cuda"))
+        ropts.append(kpm.make_rmft_opts(w.n_target, tol=0.0))
+    mu = torch.zeros(len(shapes), dtype=torch.float64, device="cuda")
+    kpm.rmft_iterate_batched(ctx, models, kpm.make_opts(64, kpm.KPM_FP32), ropts, phis, params, mu, 1)
+    torch.cuda.synchronize()
+    assert all(bool(torch.isfinite(p).all()) for p in params)
+    kpm.kpm_destroy(ctx)
+    print("profile-batched done")
+    return 0
+
+
 def profile_small(double_step=False):
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
     (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
@@ -985,6 +1014,8 @@ def main():
     args = parse()
     if args.profile_small:
         return profile_small(args.double_step)
+    if args.profile_batched:
+        return profile_batched()
     if args.profile_probing:
         return profile_probing()
     if args.lbfgs_study:

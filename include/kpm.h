@@ -202,8 +202,9 @@ int kpm_sync_status(kpm_ctx* ctx, void* stream);
 int kpm_inject_lost_copy(kpm_ctx* ctx, int count, double wait_limit_s);
 /* Measured ALU peaks of the device (no counterpart in the paper; the
  * denominators of the FP64 and double-float rooflines): independent FMA
- * chains, 8 per thread, 4 CTAs of 256 threads per SM, timed with CUDA events on
- * `stream`.  out[0] = FP64 FMA TFLOP/s (2 flops per FMA), out[1] = FP32 scalar
+ * chains, 8 per thread, 4 CTAs of 256 threads per SM, the chains sharing one
+ * multiplier/addend pair or each with its own (the better of the two per
+ * kind, best of 3 launches each), timed with CUDA events on `stream`.  out[0] = FP64 FMA TFLOP/s (2 flops per FMA), out[1] = FP32 scalar
  * FMA TFLOP/s, out[2] = FP32 packed f32x2 FMA TFLOP/s (4 flops per
  * instruction), out[3] = median SM clock seen by the kernels in MHz (from
  * %clock64 over %globaltimer).  out: host, 4 doubles.  Synchronises `stream`. */

@@ -26,16 +26,23 @@ __device__ __forceinline__ void clock_stamp(unsigned long long* t) {
   t[1] = g;
 }
 
-template <typename T>
+// SPREAD: each chain has its own multiplier and addend registers; else all
+// chains share one pair (the two operand patterns favour different pipes'
+// register-bank access, so the probe keeps the better of the two)
+template <typename T, bool SPREAD>
 __global__ void __launch_bounds__(256) fma_chain_kernel(int iters, T a, T b, T* sink, unsigned long long* clk) {
   __shared__ unsigned long long t0[2];
   if (threadIdx.x == 0) clock_stamp(t0);
-  T x[kChains];
+  T x[kChains], y[kChains], z[kChains];
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) x[k] = (T)(threadIdx.x + k);
+  for (int k = 0; k < kChains; ++k) {
+    x[k] = (T)(threadIdx.x + k);
+    y[k] = SPREAD ? a + (T)k * (T)1e-9 : a;
+    z[k] = SPREAD ? b * (T)(k + 1) : b;
+  }
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = fma_rn(x[k], a, b);
+    for (int k = 0; k < kChains; ++k) x[k] = SPREAD ? fma_rn(x[k], y[k], z[k]) : fma_rn(x[k], a, b);
   }
   T s = 0;
 #pragma unroll
@@ -115,13 +122,17 @@ cudaError_t measure_alu_peaks(int sms, void* scratch, double* out, cudaStream_t 
     // flops per thread-iteration: 8 chains x 2 (x 2 packed)
     const int iters = kind == 0 ? 2048 : (kind == 1 ? 65536 : 32768);
     const double flops = threads_total * iters * kChains * (kind == 2 ? 4.0 : 2.0);
-    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 7 && e == cudaSuccess; ++rep) {
       e = cudaEventRecord(e0, s);
       if (e != cudaSuccess) break;
+      // reps 1-3 one operand pattern, 4-6 the other (rep 0 warms up)
+      const bool spread = rep >= 4;
       if (kind == 0)
-        fma_chain_kernel<double><<<grid, threads, 0, s>>>(iters, 0.9999999, 1e-7, sink, clk);
+        spread ? fma_chain_kernel<double, true><<<grid, threads, 0, s>>>(iters, 0.9999999, 1e-7, sink, clk)
+               : fma_chain_kernel<double, false><<<grid, threads, 0, s>>>(iters, 0.9999999, 1e-7, sink, clk);
       else if (kind == 1)
-        fma_chain_kernel<float><<<grid, threads, 0, s>>>(iters, 0.9999999f, 1e-7f, (float*)sink, clk);
+        spread ? fma_chain_kernel<float, true><<<grid, threads, 0, s>>>(iters, 0.9999999f, 1e-7f, (float*)sink, clk)
+               : fma_chain_kernel<float, false><<<grid, threads, 0, s>>>(iters, 0.9999999f, 1e-7f, (float*)sink, clk);
       else
         fma_chain_f32x2_kernel<<<grid, threads, 0, s>>>(iters, pack2(0.9999999f), pack2(1e-7f), (float*)sink, clk);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -130,7 +141,7 @@ cudaError_t measure_alu_peaks(int sms, void* scratch, double* out, cudaStream_t 
       float ms = 0.f;
       if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
       if (rep > 0) best[kind] = std::max(best[kind], flops / (ms * 1e-3) / 1e12);  // rep 0 warms up
-      if (kind == 1 && rep == 3) {
+      if (kind == 1 && rep == 6) {
         if ((e = cudaMemcpy(hclk.data(), clk, hclk.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost)) !=
             cudaSuccess)
           break;
