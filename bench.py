@@ -63,6 +63,8 @@ def parse():
                     help="64x64 fixed-point loop against the L-BFGS driver (field residual vs passes) and exit")
     ap.add_argument("--profile-adjoint", nargs="?", const="small", choices=["small", "full"],
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
+    ap.add_argument("--fd-study", type=int, nargs="?", const=200, default=None,
+                    help="64x64 adjoint against central finite differences on N field components (default 200), and exit")
     ap.add_argument("--cfg1-study", action="store_true",
                     help="48x24 cell to self-consistency at 1e-7 (solve.converge) against linear mixing alone, and exit")
     ap.add_argument("--profile-batched", action="store_true",
@@ -898,6 +900,86 @@ def cfg1_study(linear_budget=6000):
     return 0
 
 
+def fd_study(ncomp=200, h=1e-6):
+    """The 64x64 adjoint workload (M = 1024, L = sum_i (n_i - n_target,i)^2,
+    n_target seeded as in the configuration): the FP64 and FP32 gradients of
+    kpm_backward (regenerating from the forward pass's tail) against central
+    finite differences with step h of FP64-accurate forward passes (the
+    double-float recursion, within 1e-14 of FP64) on `ncomp` seeded field
+    components, the rescaling (a, b) held fixed."""
+    import numpy as np
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    w = inputs.CFG4
+    N, M = w.n_sites, w.M
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    nt = torch.tensor(inputs.target_density(w, seed=1), device="cuda")
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+
+    def grad(prec):
+        kpm.kpm_observables(ctx, model, kpm.make_opts(M, prec, flags=kpm.KPM_FLAG_KEEP_TAIL), fields, ab, obs)
+        n = obs[:N] + obs[N:2 * N]
+        g = torch.zeros(26 * N, dtype=torch.float64, device="cuda")
+        g[:N] = 2 * (n - nt)
+        g[N:2 * N] = 2 * (n - nt)
+        out = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        kpm.kpm_backward(ctx, model, kpm.make_opts(M, prec), fields, ab, g, 0.0, out, ckpt_every=kpm.KPM_REGENERATE)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), time.perf_counter() - t0
+
+    g64, t64 = grad(kpm.KPM_FP64)
+    g32, t32 = grad(kpm.KPM_FP32)
+    odf = kpm.make_opts(M, kpm.KPM_DF64)
+
+    def L(f):
+        kpm.kpm_observables(ctx, model, odf, f, ab, obs)
+        n = obs[:N] + obs[N:2 * N]
+        return float(((n - nt) ** 2).sum())
+
+    rng = np.random.default_rng(1)
+    comps = np.sort(rng.choice(26 * N, size=ncomp, replace=False))
+    rows = []
+    t0 = time.perf_counter()
+    for k in comps:
+        f = fields.clone()
+        f[int(k)] += h
+        lp = L(f)
+        f[int(k)] -= 2 * h
+        lm = L(f)
+        rows.append((int(k), (lp - lm) / (2 * h), float(g64[k]), float(g32[k])))
+    tfd = time.perf_counter() - t0
+    fd = np.array([r[1] for r in rows])
+    a64 = np.array([r[2] for r in rows])
+    a32 = np.array([r[3] for r in rows])
+    scale = float(np.max(np.abs(g64)))
+    big = np.abs(a64) >= 1e-3 * scale
+    rel64 = np.abs(fd - a64) / np.maximum(np.abs(a64), 1e-300)
+    rel32 = np.abs(fd - a32) / np.maximum(np.abs(a64), 1e-300)
+    out = {"cell": "64x64", "M": M, "h": h, "components": int(ncomp), "seed": 1,
+           "forward": "double-float recursion (FP64-accurate), a and b fixed",
+           "gradient": "kpm_backward, regenerating from the forward pass's tail",
+           "max_abs_grad": scale, "components_above_1e-3_of_max": int(big.sum()),
+           "fp64_max_rel_err_above_1e-3": float(rel64[big].max()) if big.any() else None,
+           "fp64_max_abs_err_over_max_grad": float(np.max(np.abs(fd - a64)) / scale),
+           "fp32_max_rel_err_above_1e-3": float(rel32[big].max()) if big.any() else None,
+           "fp32_max_abs_err_over_max_grad": float(np.max(np.abs(fd - a32)) / scale),
+           "backward_fp64_s": t64, "backward_fp32_s": t32, "fd_s": tfd,
+           "rows_index_fd_fp64_fp32": rows}
+    kpm.kpm_destroy(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def profile_adjoint(full=False):
     """Adjoint case for ncu: the 64x64 cell, FP32.  Small (default): M = 64,
     checkpoints every 8 moments, slabs of 2048 columns (134 MB per slab
@@ -1022,6 +1104,8 @@ def main():
         return lbfgs_study()
     if args.cfg1_study:
         return cfg1_study()
+    if args.fd_study is not None:
+        return fd_study(args.fd_study)
     if args.profile_adjoint:
         return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":

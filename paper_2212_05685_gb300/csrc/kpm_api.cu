@@ -936,6 +936,12 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   if ((r = ensure_pass_scratch(ctx, model, &o, pp))) return r;
   const ChebPlan& p = pp.cheb;
   const size_t vbytes = (size_t)D * p.ldv * elem;
+  if (use_tail) {
+    // the tail is read slab by slab: only with the forward pass's exact slabs
+    const int64_t nslab = (pp.c1 - pp.c0 + pp.width - 1) / pp.width;
+    use_tail = pp.width == ctx->tail_width && pp.c0 == ctx->tail_c0 && pp.c1 == ctx->tail_c1 &&
+               (size_t)(2 * nslab) * vbytes <= ctx->tail_bytes;
+  }
   if ((r = ensure(ctx, &ctx->bwd, &ctx->bwd_bytes, vbytes * (size_t)nvec))) return r;
   const int groups = grad_groups(p, o.precision);
   const size_t gbytes = (size_t)D * 13 * sizeof(double2);  // G, then the column sets' partial sums
@@ -945,8 +951,10 @@ int kpm_backward(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   char* base = static_cast<char*>(ctx->bwd);
   auto ckpt = [&](int k) { return (void*)(base + vbytes * (size_t)k); };
   auto segv = [&](int j) { return (void*)(base + vbytes * (size_t)(2 * K + j)); };
-  void* lamA = base + vbytes * (size_t)(2 * K + seg);
-  void* lamB = base + vbytes * (size_t)(2 * K + seg + 1);
+  // the lambda pair: the last two of the nvec vectors (checkpoints and the
+  // segment first when checkpointing; alone when regenerating)
+  void* lamA = base + vbytes * (size_t)(nvec - 2);
+  void* lamB = base + vbytes * (size_t)(nvec - 1);
 
   cudaStream_t s = (cudaStream_t)stream;
   const int prec = o.precision;

@@ -216,7 +216,16 @@ def test_regenerate_matches_oracle(K, nx, ny, M, bw, prec):
     model, phi, params, fields, ab = _prep(K, nx, ny, p)
     rng = np.random.default_rng(nx + ny)
     g_obs, g_om = rng.normal(size=26 * nx * ny), 0.4
-    got, _ = _gpu_grad(K, model, fields, ab, M, prec, g_obs, g_om, bw=bw, ckpt=kpm.KPM_REGENERATE)
+    # a fresh context: its scratch holds exactly what this mode asks for
+    fresh = kpm.kpm_create(0)
+    try:
+        out = torch.empty(26 * nx * ny, dtype=torch.float64, device="cuda")
+        kpm.kpm_backward(fresh, model, kpm.make_opts(M, prec, bw), fields, ab, dev(g_obs), g_om, out,
+                         ckpt_every=kpm.KPM_REGENERATE)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+    finally:
+        kpm.kpm_destroy(fresh)
     ref = adjoint.vjp_dense(rmft.Model(nx, ny), fields.cpu().numpy(), *ab.cpu().numpy(), M, g_obs, g_om)
     tol = 1e-10 if prec == 0 else 2e-5
     assert np.max(np.abs(got - ref)) < tol * max(1.0, np.max(np.abs(ref)))
@@ -228,11 +237,12 @@ def test_regenerate_from_kept_tail(K, prec):
     of every slab; the regenerating backward pass on the same fields then runs
     no forward sweep and gives the same bits as with its own sweep; after the
     fields change the tail is not used (the gradient follows the new fields)."""
-    kpm, ctx = K
+    kpm, _ = K
     nx, ny, M = 10, 8, 80
     N = nx * ny
     w = inputs.Workload(nx, ny, 0.15, inputs.two_vortex(nx, ny), M, seed=2)
     model, phi, params, fields, ab = _prep(K, nx, ny, inputs.vortex_seed(w))
+    ctx = kpm.kpm_create(0)  # fresh scratch, sized by this mode alone
     g = dev(np.random.default_rng(4).normal(size=26 * N))
     obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
     opts = kpm.make_opts(M, prec, 48)
@@ -254,6 +264,7 @@ def test_regenerate_from_kept_tail(K, prec):
     ref = adjoint.vjp_dense(rmft.Model(nx, ny), fields2.cpu().numpy(), *ab.cpu().numpy(), M, g.cpu().numpy(), 0.3)
     tol = 1e-10 if prec == 0 else 2e-5
     assert np.max(np.abs(new.cpu().numpy() - ref)) < tol * max(1.0, np.max(np.abs(ref)))
+    kpm.kpm_destroy(ctx)
 
 
 def test_autograd_regenerates_from_forward_tail(K):
