@@ -65,12 +65,19 @@ def parse():
                     help="run the adjoint case used for ncu captures (small, or the benchmarked full pass) and exit")
     ap.add_argument("--fd-study", type=int, nargs="?", const=200, default=None,
                     help="64x64 adjoint against central finite differences on N field components (default 200), and exit")
+    ap.add_argument("--fd-forward", choices=["df64", "fp64"], default="df64",
+                    help="recursion of the finite-difference forward passes of --fd-study")
     ap.add_argument("--cfg1-study", action="store_true",
                     help="48x24 cell to self-consistency at 1e-7 (solve.converge) against linear mixing alone, and exit")
     ap.add_argument("--profile-batched", action="store_true",
                     help="one batched iteration (4 cells 48x24 and 2 cells 64x32, M=64, FP32) for ncu captures")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
+    ap.add_argument("--batched-study", action="store_true",
+                    help="the batched section alone (32 cells 24x12 .. 64x32, M=1024), and exit")
+    ap.add_argument("--width-study", type=int, nargs="?", const=0, default=None,
+                    help="per-step recursion rate against the slab width (full and half pass) on the 100x100 cell; "
+                         "with a width, one half pass at that width and M=8 for ncu captures")
     return ap.parse_args()
 
 
@@ -300,7 +307,7 @@ def run_ours(args):
         kpm.kpm_bounds(ctx, model, f0, 0.01, ab0)
         t0 = time.perf_counter()
         opts, ms_step = kpm.kpm_autotune(ctx, model, opts, f0, ab0)
-        tune = {"block_width": opts.block_width, "cols_per_block": opts.cols_per_block,
+        tune = {"block_width": opts.block_width, "cols_per_block": opts.cols_per_block, "band_rows": opts.band_rows,
                 "trial_ms_per_step": ms_step, "tuning_s": time.perf_counter() - t0}
         del f0, ab0
 
@@ -503,7 +510,8 @@ def run_ours(args):
                    "speedup_vs_full_pass": (t / args.steps) / th,
                    "recursion_achieved_gbs": hb / (hm / 1e3) / 1e9,
                    "columns": f"{N} of {D} unit columns (j, up); the (j, dn) observables from the particle-hole relation",
-                   "flags": oh.flags, "block_width": oh.block_width, "cols_per_block": oh.cols_per_block}
+                   "flags": oh.flags, "block_width": oh.block_width, "cols_per_block": oh.cols_per_block,
+                   "band_rows": oh.band_rows}
 
     probe = None if args.no_probing else probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch)
     ldos_res = None if args.no_ldos else ldos_section(kpm, ctx, model, phi, torch.tensor(p0, device="cuda"), torch)
@@ -672,7 +680,7 @@ def probing_section(kpm, ctx, model, phi, params, M, ropts, p0, args, torch):
         ev[1].record()
         torch.cuda.synchronize()
         rows.append({"p": p, "R": 2 * p * p, "s_per_pass": t_pass, "cols_per_block": o.cols_per_block,
-                     "two_steps_per_launch": bool(o.flags & kpm.KPM_FLAG_DOUBLE_STEP),
+                     "band_rows": o.band_rows, "two_steps_per_launch": bool(o.flags & kpm.KPM_FLAG_DOUBLE_STEP),
                      "s_per_rmft_iteration": ev[0].elapsed_time(ev[1]) / 1e3 / args.steps,
                      "max_err_n": float(d[:2 * N].max()), "max_err_chi": float(d[2 * N:18 * N].max()),
                      "max_err_F": float(d[18 * N:].max())})
@@ -900,13 +908,14 @@ def cfg1_study(linear_budget=6000):
     return 0
 
 
-def fd_study(ncomp=200, h=1e-6):
+def fd_study(ncomp=200, h=1e-6, forward="df64"):
     """The 64x64 adjoint workload (M = 1024, L = sum_i (n_i - n_target,i)^2,
     n_target seeded as in the configuration): the FP64 and FP32 gradients of
     kpm_backward (regenerating from the forward pass's tail) against central
     finite differences with step h of FP64-accurate forward passes (the
-    double-float recursion, within 1e-14 of FP64) on `ncomp` seeded field
-    components, the rescaling (a, b) held fixed."""
+    double-float recursion, or with forward="fp64" the FP64 one, whose
+    rounding noise divided by h is the floor of the comparison) on `ncomp`
+    seeded field components, the rescaling (a, b) held fixed."""
     import numpy as np
     import torch
     from paper_2212_05685_gb300 import build, inputs, kpm
@@ -939,7 +948,7 @@ def fd_study(ncomp=200, h=1e-6):
 
     g64, t64 = grad(kpm.KPM_FP64)
     g32, t32 = grad(kpm.KPM_FP32)
-    odf = kpm.make_opts(M, kpm.KPM_DF64)
+    odf = kpm.make_opts(M, kpm.KPM_FP64 if forward == "fp64" else kpm.KPM_DF64)
 
     def L(f):
         kpm.kpm_observables(ctx, model, odf, f, ab, obs)
@@ -966,7 +975,9 @@ def fd_study(ncomp=200, h=1e-6):
     rel64 = np.abs(fd - a64) / np.maximum(np.abs(a64), 1e-300)
     rel32 = np.abs(fd - a32) / np.maximum(np.abs(a64), 1e-300)
     out = {"cell": "64x64", "M": M, "h": h, "components": int(ncomp), "seed": 1,
-           "forward": "double-float recursion (FP64-accurate), a and b fixed",
+           "forward": ("FP64 recursion" if forward == "fp64" else "double-float recursion (FP64-accurate)")
+                      + ", a and b fixed",
+           "fd_abs_err_median": float(np.median(np.abs(fd - a64))),
            "gradient": "kpm_backward, regenerating from the forward pass's tail",
            "max_abs_grad": scale, "components_above_1e-3_of_max": int(big.sum()),
            "fp64_max_rel_err_above_1e-3": float(rel64[big].max()) if big.any() else None,
@@ -1092,8 +1103,101 @@ def profile_small(double_step=False):
     return 0
 
 
+def width_study(half_width=0):
+    """Per-step rate of the FP32 recursion on the benchmark lattice against the
+    slab width, for the full pass and the particle-hole half pass: each
+    configuration runs two passes of different order (M = 66 and 194), so the
+    difference is the time of 128 steps per slab without the per-slab start
+    and gather.  With half_width > 0, one half pass at that width and M = 8
+    (for ncu) instead."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    w = inputs.CFG2
+    N, D = w.n_sites, w.dim
+    ctx = kpm.kpm_create(0)
+    model = kpm.make_model(w.nx, w.ny)
+    phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_peierls_phases(ctx, model, phi)
+    params = torch.tensor(inputs.vortex_seed(w), device="cuda")
+    fields = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+    kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
+    kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
+    ab[1] = 0.0  # the half pass needs the centre at 0; the full pass takes it too
+    if half_width:
+        kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, half_width, 16, flags=kpm.KPM_FLAG_PH_HALF),
+                            fields, ab, obs)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(obs).all())
+        kpm.kpm_destroy(ctx)
+        print("width-study half pass done")
+        return 0
+    stream = torch.cuda.current_stream()
+    M1, M2 = 66, 194
+    rows = []
+
+    def timed(o):
+        kpm.kpm_observables(ctx, model, o, fields, ab, obs)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(2):
+            e0.record(stream)
+            kpm.kpm_observables(ctx, model, o, fields, ab, obs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    configs = []
+    for half, ncols, widths in ((0, D, (20000, 10000, 4000, 2000)), (1, D // 2, (10000, 5000, 2500))):
+        for width in widths:
+            configs.append((half, 0, ncols, width, kpm.KPM_FLAG_DOUBLE_STEP, 0))
+            for band in (0, 10, 20, 25, 34, 50, 100):
+                configs.append((half, 0, ncols, width, 0, band))
+    for band in (0, 2, 3, 4, 5, 7, 9, 10, 12):
+        configs.append((0, 10, 2 * 10 * 10, 2 * 10 * 10, 0, band))
+    for half, probe, ncols, width, dbl, band in configs:
+        flags = dbl | (kpm.KPM_FLAG_PH_HALF if half else 0)
+        t1 = timed(kpm.make_opts(M1, kpm.KPM_FP32, width, 16, flags=flags, probe_p=probe, band_rows=band))
+        t2 = timed(kpm.make_opts(M2, kpm.KPM_FP32, width, 16, flags=flags, probe_p=probe, band_rows=band))
+        ldv = (width + 15) // 16 * 16
+        nslab = -(-ncols // width)
+        step = (t2 - t1) / (nslab * (M2 - M1))
+        over = (t1 - nslab * (M1 - 1) * step) / nslab
+        gbs = 3 * D * ldv * 8 / step / 1e9
+        rows.append({"pass": "probing p=10" if probe else ("half" if half else "full"), "width": width,
+                     "two_steps_per_launch": bool(dbl), "band_rows": band, "slabs": nslab,
+                     "ms_per_step": step * 1e3, "stream_gbs": gbs, "ms_start_gather_per_slab": over * 1e3,
+                     "s_per_pass_M2048": nslab * (over + 2047 * step)})
+    print(json.dumps({"study": "slab width and band height", "cell": "100x100", "cols_per_block": 16,
+                      "M": [M1, M2], "bytes_per_step": "3 D ldv 8 (read V_m, V_m-1, write V_m+1)",
+                      "band_rows": "0 = library default", "rows": rows}), flush=True)
+    kpm.kpm_destroy(ctx)
+    return 0
+
+
+def batched_study():
+    """The batched section alone (32-cell mix, M = 1024), with the measured
+    FMA rates for its roofline."""
+    import torch
+    from paper_2212_05685_gb300 import build, inputs, kpm
+    build.build()
+    ctx = kpm.kpm_create(0)
+    alu = kpm.kpm_measure_peaks(ctx)
+    kpm.kpm_destroy(ctx)
+    print(json.dumps({"study": "batched", "batched": batched_section(kpm, inputs, torch, alu)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.batched_study:
+        return batched_study()
+    if args.width_study is not None:
+        return width_study(args.width_study)
     if args.profile_small:
         return profile_small(args.double_step)
     if args.profile_batched:
@@ -1105,7 +1209,7 @@ def main():
     if args.cfg1_study:
         return cfg1_study()
     if args.fd_study is not None:
-        return fd_study(args.fd_study)
+        return fd_study(args.fd_study, forward=args.fd_forward)
     if args.profile_adjoint:
         return profile_adjoint(args.profile_adjoint == "full")
     if args.impl == "reference":

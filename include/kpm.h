@@ -104,7 +104,11 @@ typedef struct {
                            sites sum to the full pass exactly and the omegas to rounding.
                            kpm_observables and kpm_backward (its gradient is then the part
                            from those columns); with probing, KPM_EINVAL. */
-  int32_t reserved;     /* 0 */
+  int32_t band_rows;    /* lattice rows per CTA of the one-step recursion kernels (each
+                           CTA runs a band of rows of one column chunk); 0 = the
+                           library's choice, else min(band_rows, ny).  Changes the
+                           launch shape only, not the result; kpm_autotune searches
+                           it.  Negative: KPM_EINVAL. */
 } kpm_opts;
 
 /* kpm_opts.flags: run the FP32 recursion two steps per launch where the
@@ -281,15 +285,20 @@ int rmft_prepare(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
 int rmft_update(kpm_ctx* ctx, const kpm_model* model, const kpm_rmft_opts* ropts, double* params, double* obs,
                 double* mu_eff, double* stats_out, void* stream);
 
-/* Autotuner of the recursion launch: times a short pass (M = 32) for every
- * slab width in {D, 8192, ..., 128} (narrow slabs keep both recursion
- * vectors in L2), every column chunk that fits shared memory and (FP32) one
- * or two steps per launch, and writes the fastest (block_width,
- * cols_per_block, KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields
- * copied from *opts).  Results are cached per (nx, ny, precision,
- * KPM_FLAG_PH_HALF, probe_p) in the context
- * (a cached answer returns *best_ms_per_step = -1).  fields, ab: device, as
- * for kpm_observables.  best_ms_per_step: host double or NULL. */
+/* Autotuner of the recursion launch: times two short passes (M = 18 and 34)
+ * for every slab width in {D, 8192, ..., 128} (narrow slabs keep both
+ * recursion vectors in L2), every column chunk that fits shared memory and
+ * (FP32) one or two steps per launch, and for one step per launch the
+ * default band height and the two best of a wave model of the launch (CTAs
+ * of ceil(ny / bands) rows, one per SM), predicts the pass at opts->M from the
+ * line through both times (per-slab start and gather plus M - 1 steps), and
+ * writes the fastest (block_width, cols_per_block, band_rows,
+ * KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields copied from
+ * *opts).  Results are cached per
+ * (nx, ny, precision, KPM_FLAG_PH_HALF, probe_p, M) in the context (a cached
+ * answer returns *best_ms_per_step = -1).  fields, ab: device, as for
+ * kpm_observables.  best_ms_per_step: host double or NULL, the chosen
+ * configuration's time per moment of the whole pass (all slabs), in ms. */
 int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, const double* fields,
                  const double* ab, kpm_opts* best, double* best_ms_per_step, void* stream);
 

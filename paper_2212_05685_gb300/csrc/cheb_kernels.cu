@@ -37,6 +37,8 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "kpm_internal.cuh"
 
@@ -450,6 +452,16 @@ __device__ __forceinline__ int nambu_slot(int x, int al) {
   return SW ? (al ^ (x & 1)) : al;
 }
 
+// Order of the terms of one output row: the nine stencil positions row by
+// row (lattice row y-1, y, y+1; x-1, x, x+1 in each), at each neighbour its
+// hopping entry and, for the four nearest neighbours, its pairing entry.  Every
+// FP32 kernel accumulates in this order, so all of them (one or two steps per
+// launch, streaming or persistent, one or two sites per thread) give the same
+// bits.  Position p = 3 (dy + 1) + (dx + 1) -> neighbour index k of the table
+// entries (1 + k, 9 + k hopping; 17 + k, 21 + k pairing for k < 4), -1 = the
+// site itself (the real diagonals, entry 0)
+__device__ constexpr int kPosK[9] = {5, 3, 6, 1, -1, 0, 7, 2, 4};
+
 template <int NV, bool SW = false>
 __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0, const float4* wp,
                                              const float2* cf_row, int x, int nx, ulonglong2& o0, ulonglong2& o1) {
@@ -460,27 +472,28 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
 #define KPM_L(W, XX, AL) \
   (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + nambu_slot<NV, SW>((XX), (AL)) * NV))
   Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
-  {
-    const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
-    const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
-    const u64 d0 = dup2(d.x), d1 = dup2(d.y);
-    a0.pr = f2fma(d0, u0.x, a0.pr);
-    a0.pi = f2fma(d0, u0.y, a0.pi);
-    a1.pr = f2fma(d1, u1.x, a1.pr);
-    a1.pi = f2fma(d1, u1.y, a1.pi);
-  }
-  // neighbours k = 1..8: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1)
-  const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
-  const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
+  const float4* wr[3] = {wm, w0, wp};
+  const int xs[3] = {xl, x, xr};
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
-    const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
-    acc_term(a0, cf[1 + k], u0);
-    acc_term(a1, cf[9 + k], u1);
-    if (k < 4) {
-      acc_term(a0, cf[17 + k], u1);
-      acc_term(a1, cf[21 + k], u0);
+  for (int pos = 0; pos < 9; ++pos) {
+    const int k = kPosK[pos];
+    const float4* W = wr[pos / 3];
+    const int xx = xs[pos % 3];
+    const ulonglong2 u0 = KPM_L(W, xx, 0), u1 = KPM_L(W, xx, 1);
+    if (k < 0) {
+      const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
+      const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+      a0.pr = f2fma(d0, u0.x, a0.pr);
+      a0.pi = f2fma(d0, u0.y, a0.pi);
+      a1.pr = f2fma(d1, u1.x, a1.pr);
+      a1.pi = f2fma(d1, u1.y, a1.pi);
+    } else {
+      acc_term(a0, cf[1 + k], u0);
+      acc_term(a1, cf[9 + k], u1);
+      if (k < 4) {
+        acc_term(a0, cf[17 + k], u1);
+        acc_term(a1, cf[21 + k], u0);
+      }
     }
   }
 #undef KPM_L
@@ -488,58 +501,88 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
   o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
 }
 
-// The same stencil with the site's entries read as 16-byte pairs: half the
-// load instructions for the coefficients and the same arithmetic in the same
-// order (bit-identical); the persistent kernel, bound by its shared-memory
-// instructions, uses it (in the streaming step it measured 0.4% slower)
+// The persistent kernel keeps a site's entries in the order the terms use
+// them: kCoefOrder[i] = table entry at stored position i (entry 0 holds both
+// real diagonals; the last position is padding)
+__constant__ int kCoefOrder[kCoef] = {6,  14, 4,  12, 20, 24, 7,  15,         // row y-1
+                                      2,  10, 18, 22, 0,  1,  9,  17, 21,     // row y
+                                      8,  16, 3,  11, 19, 23, 5,  13, 25};    // row y+1
+
+// Two neighbouring sites x and x + 1 of one lattice row for one column pair
+// (both Nambu rows each), the same terms in the same order as stencil_site:
+// the four V_m positions x-1 .. x+2 of each row are loaded once for both
+// sites (24 instead of 36 loads).  cqA, cqB: the two sites' entries in
+// kCoefOrder order as 16-byte pairs.
 template <int NV>
-__device__ __forceinline__ void stencil_site_paired(const float4* wm, const float4* w0, const float4* wp,
-                                             const float2* cf_row, int x, int nx, ulonglong2& o0, ulonglong2& o1) {
+__device__ __forceinline__ void stencil_2site(const float4* wm, const float4* w0, const float4* wp,
+                                              const float4* cqA, const float4* cqB, int x, int nx,
+                                              ulonglong2& oA0, ulonglong2& oA1, ulonglong2& oB0, ulonglong2& oB1) {
   constexpr int RS = 2 * NV;
-  const int xr = x + 1 == nx ? 0 : x + 1;
-  const int xl = x == 0 ? nx - 1 : x - 1;
-  // the site's kCoef entries as 16-byte pairs (kCoef even, rows 16-byte aligned):
-  // entry e is half (e & 1) of pair e >> 1
-  const float4* cq = reinterpret_cast<const float4*>(cf_row + x * kCoef);
-#define KPM_L(W, XX, AL) \
-  (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + nambu_slot<NV, false>((XX), (AL)) * NV))
-#define KPM_C(Q, E) ((E) & 1 ? make_float2((Q).z, (Q).w) : make_float2((Q).x, (Q).y))
-  Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
-  const float4 q0 = cq[0];  // entries 0 (diagonals) and 1
-  {
-    const float2 d = KPM_C(q0, 0);  // (d0, d1): real diagonals of the two Nambu rows
-    const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
-    const u64 d0 = dup2(d.x), d1 = dup2(d.y);
-    a0.pr = f2fma(d0, u0.x, a0.pr);
-    a0.pi = f2fma(d0, u0.y, a0.pi);
-    a1.pr = f2fma(d1, u1.x, a1.pr);
-    a1.pi = f2fma(d1, u1.y, a1.pi);
-  }
-  // neighbours k = 1..8: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1);
-  // the entries of two neighbours at a time (pairs of e = 1 + k, 9 + k, 17 + k, 21 + k)
-  const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
-  const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
-  float4 h0 = q0, h1, p0, p1;
+  // x-1, x, x+1, x+2 (periodic)
+  int xs[4];
+  xs[0] = x == 0 ? nx - 1 : x - 1;
+  xs[1] = x;
+  xs[2] = x + 1 >= nx ? x + 1 - nx : x + 1;
+  xs[3] = x + 2 >= nx ? x + 2 - nx : x + 2;
+  Acc2 A0 = {0ull, 0ull, 0ull, 0ull}, A1 = {0ull, 0ull, 0ull, 0ull};
+  Acc2 B0 = {0ull, 0ull, 0ull, 0ull}, B1 = {0ull, 0ull, 0ull, 0ull};
+  const float4* wr[3] = {wm, w0, wp};
+  float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
+  // stored entry i of a site: half (i & 1) of pair i >> 1, loaded when first needed
+  auto ent = [](const float4& q, int i) { return (i & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y); };
+  // one term of site S (0 = A, 1 = B) at stored position i
+  auto term = [&](Acc2& a, int S, int i, ulonglong2 u) {
+    if ((i & 1) == 0) {
+      if (S == 0) qa = cqA[i >> 1]; else qb = cqB[i >> 1];
+    }
+    acc_term(a, ent(S == 0 ? qa : qb, i), u);
+  };
+  // stored position of the first entry of stencil position pos (row-major)
+  constexpr int kFirst[9] = {0, 2, 6, 8, 12, 13, 17, 19, 23};
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    // pair holding entry 1 + k: (1 + k) >> 1; 9 + k: (9 + k) >> 1; ...
-    if (k > 0 && ((1 + k) & 1) == 0) h0 = cq[(1 + k) >> 1];
-    if (((9 + k) & 1) == 0 || k == 0) h1 = cq[(9 + k) >> 1];
-    if (k < 4 && (((17 + k) & 1) == 0 || k == 0)) p0 = cq[(17 + k) >> 1];
-    if (k < 4 && (((21 + k) & 1) == 0 || k == 0)) p1 = cq[(21 + k) >> 1];
-    const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
-    const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
-    acc_term(a0, KPM_C(h0, 1 + k), u0);
-    acc_term(a1, KPM_C(h1, 9 + k), u1);
-    if (k < 4) {
-      acc_term(a0, KPM_C(p0, 17 + k), u1);
-      acc_term(a1, KPM_C(p1, 21 + k), u0);
+  for (int row = 0; row < 3; ++row) {
+    const float4* W = wr[row];
+    ulonglong2 u[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      u[j][0] = *reinterpret_cast<const ulonglong2*>(W + xs[j] * RS);
+      u[j][1] = *reinterpret_cast<const ulonglong2*>(W + xs[j] * RS + NV);
+    }
+#pragma unroll
+    for (int S = 0; S < 2; ++S) {
+      Acc2& a0 = S == 0 ? A0 : B0;
+      Acc2& a1 = S == 0 ? A1 : B1;
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int pos = 3 * row + dx;
+        const int k = kPosK[pos];
+        const ulonglong2 u0 = u[S + dx][0], u1 = u[S + dx][1];
+        const int i = kFirst[pos];
+        if (k < 0) {
+          if ((i & 1) == 0) {
+            if (S == 0) qa = cqA[i >> 1]; else qb = cqB[i >> 1];
+          }
+          const float2 d = ent(S == 0 ? qa : qb, i);
+          const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+          a0.pr = f2fma(d0, u0.x, a0.pr);
+          a0.pi = f2fma(d0, u0.y, a0.pi);
+          a1.pr = f2fma(d1, u1.x, a1.pr);
+          a1.pi = f2fma(d1, u1.y, a1.pi);
+        } else {
+          term(a0, S, i, u0);
+          term(a1, S, i + 1, u1);
+          if (k < 4) {
+            term(a0, S, i + 2, u1);
+            term(a1, S, i + 3, u0);
+          }
+        }
+      }
     }
   }
-#undef KPM_C
-#undef KPM_L
-  o0 = make_ulonglong2(f2sub(a0.pr, a0.qi), f2add(a0.pi, a0.qr));
-  o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
+  oA0 = make_ulonglong2(f2sub(A0.pr, A0.qi), f2add(A0.pi, A0.qr));
+  oA1 = make_ulonglong2(f2sub(A1.pr, A1.qi), f2add(A1.pi, A1.qr));
+  oB0 = make_ulonglong2(f2sub(B0.pr, B0.qi), f2add(B0.pi, B0.qr));
+  oB1 = make_ulonglong2(f2sub(B1.pr, B1.qi), f2add(B1.pi, B1.qr));
 }
 
 // moment sums acc[J][s] += a V[K_s(J), J] for the columns of the chunk whose
@@ -1437,10 +1480,13 @@ __global__ void __cluster_dims__(kPClu, 1, 1) __launch_bounds__(512, 1)
 
     // coefficients of the band; V_0 = the chunk's unit vectors; a_0 moment terms
     {
-      const float4* src = reinterpret_cast<const float4*>(cell.table + (int64_t)y0 * nx * kCoef);
-      float4* dst = reinterpret_cast<float4*>(coef);
-      const int n4 = nrow * nx * kCoef / 2;
-      for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = src[t];
+      // each site's entries in the order the stencil uses them (kCoefOrder)
+      const float2* src = cell.table + (int64_t)y0 * nx * kCoef;
+      const int n2 = nrow * nx * kCoef;
+      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int site = t / kCoef;
+        coef[t] = src[site * kCoef + kCoefOrder[t - site * kCoef]];
+      }
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int t = threadIdx.x; t < nrow * rowsz; t += blockDim.x) V0buf[t] = z4;
       if (nrow > 0)
@@ -1494,60 +1540,83 @@ __global__ void __cluster_dims__(kPClu, 1, 1) __launch_bounds__(512, 1)
         cp_async16_cg(halo + t, t < rowsz ? ga + t : gb + (t - rowsz));
       cp_commit();
     };
-    // moment sums a_m V_m of the chunk's columns whose own site is in the band
-    auto sums = [&](const float4* cur, int m) {
-      const double cm = cell.am[m], co = cell.ao[m];
-      for (int t = threadIdx.x; t < kPCB * kSlots; t += blockDim.x) {
-        const int c = t / kSlots, s = t - c * kSlots;
-        const int64_t J = q0 + c;
-        if (J >= D) continue;
-        const int64_t j = J >> 1;
-        const int y = (int)(j / nx);
-        if (y < y0 || y >= y1) continue;
+    // moment sums a_m V_m of the chunk's columns whose own site is in the band:
+    // thread t < kPCB kSlots owns entry (column c, slot s); where that entry
+    // sits in shared memory is the same for every step of the item, so it is
+    // worked out once: scode = -1 (column outside the band or the lattice),
+    // else (float4 index << 1) | (1 if in the halo rows, 0 if in the V_m band)
+    int scode = -1;
+    if (threadIdx.x < kPCB * kSlots) {
+      const int t = threadIdx.x, c = t / kSlots, s = t - c * kSlots;
+      const int64_t J = q0 + c;
+      const int64_t j = J >> 1;
+      const int y = J < D ? (int)(j / nx) : -1;
+      if (y >= y0 && y < y1) {
         const int beta = (int)(J & 1);
         const int xsl = wrapi((int)(j % nx) + kSlotDx[s], nx);
         const int al = kSlotFlip[s] ? 1 - beta : beta;
         const int r = y - y0, dy = kSlotDy[s];
-        const float4* w = dy < 0 ? row_below(cur, r) : (dy > 0 ? row_above(cur, r) : cur + (size_t)r * rowsz);
-        const float2 val = pair_elem(w + xsl * 2 * kPNV + al * kPNV, c);
-        acc_add_unit(acc + t, s == kSlots - 1 ? co : cm, (double)val.x, (double)val.y);
+        const int e = xsl * 2 * kPNV + al * kPNV + (c >> 1);
+        if (dy < 0 && r == 0) scode = (e << 1) | 1;                   // row y0 - 1: halo row 0
+        else if (dy > 0 && r + 1 == nrow) scode = ((rowsz + e) << 1) | 1;  // row y1: halo row 1
+        else scode = (((r + dy) * rowsz + e) << 1);
       }
+    }
+    auto sums = [&](const float4* cur, int m) {
+      if (scode < 0) return;
+      const int t = threadIdx.x, c = t / kSlots, s = t - c * kSlots;
+      const double cm = cell.am[m], co = cell.ao[m];
+      const float4 q = ((scode & 1) ? halo : cur)[scode >> 1];
+      const float2 val = (c & 1) ? make_float2(q.y, q.w) : make_float2(q.x, q.z);
+      acc_add_unit(acc + t, s == kSlots - 1 ? co : cm, (double)val.x, (double)val.y);
     };
 
     const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
     const int v = threadIdx.x % kPNV;
     const int gstep = blockDim.x / kPNV;
-    // band rows [r0, r1) of V_{m+1}; boundary rows also go to the exchange slots
-    auto rows = [&](const float4* cur, float4* out, int m, int r0, int r1) {
-      const int nr = r1 - r0;
-      for (int t = threadIdx.x / kPNV; t < nr * nx; t += gstep) {
-        const int r = r0 + t / nx, x = t - (r - r0) * nx;
-        ulonglong2 o0, o1;
-        stencil_site_paired<kPNV>(row_below(cur, r) + v, cur + (size_t)r * rowsz + v, row_above(cur, r) + v,
-                                  coef + (size_t)r * nx * kCoef, x, nx, o0, o1);
-        const size_t off = (size_t)x * 2 * kPNV + v;
-        ulonglong2* g = reinterpret_cast<ulonglong2*>(out + (size_t)r * rowsz + off);
-        if (m == 0) {
-          o0.x = f2mul(o0.x, half2);
-          o0.y = f2mul(o0.y, half2);
-          o1.x = f2mul(o1.x, half2);
-          o1.y = f2mul(o1.y, half2);
-        } else {
-          const ulonglong2 p0 = g[0], p1 = g[kPNV];
-          o0.x = f2sub(o0.x, p0.x);
-          o0.y = f2sub(o0.y, p0.y);
-          o1.x = f2sub(o1.x, p1.x);
-          o1.y = f2sub(o1.y, p1.y);
+    // V_{m+1} of site x of band row r from 2h~ V_m (o0, o1): halved at m = 0,
+    // else minus V_{m-1} (stored where V_{m+1} goes); boundary rows also go
+    // to the exchange slots
+    auto emit = [&](float4* out, int m, int r, int x, ulonglong2 o0, ulonglong2 o1) {
+      const size_t off = (size_t)x * 2 * kPNV + v;
+      ulonglong2* g = reinterpret_cast<ulonglong2*>(out + (size_t)r * rowsz + off);
+      if (m == 0) {
+        o0.x = f2mul(o0.x, half2);
+        o0.y = f2mul(o0.y, half2);
+        o1.x = f2mul(o1.x, half2);
+        o1.y = f2mul(o1.y, half2);
+      } else {
+        const ulonglong2 p0 = g[0], p1 = g[kPNV];
+        o0.x = f2sub(o0.x, p0.x);
+        o0.y = f2sub(o0.y, p0.y);
+        o1.x = f2sub(o1.x, p1.x);
+        o1.y = f2sub(o1.y, p1.y);
+      }
+      g[0] = o0;
+      g[kPNV] = o1;
+      const int p = (m + 1) & 1;
+      for (int h = 0; h < 2; ++h)
+        if (r == (h == 0 ? 0 : nrow - 1)) {
+          ulonglong2* e = reinterpret_cast<ulonglong2*>(xslot(rank, h, p) + off);
+          e[0] = o0;
+          e[kPNV] = o1;
         }
-        g[0] = o0;
-        g[kPNV] = o1;
-        const int p = (m + 1) & 1;
-        for (int h = 0; h < 2; ++h)
-          if (r == (h == 0 ? 0 : nrow - 1)) {
-            ulonglong2* e = reinterpret_cast<ulonglong2*>(xslot(rank, h, p) + off);
-            e[0] = o0;
-            e[kPNV] = o1;
-          }
+    };
+    // band rows r0, r0 + rstep, ... (< r1) of V_{m+1}, two neighbouring sites
+    // of a row per thread and column pair
+    const int npair = (nx + 1) >> 1;
+    auto rows = [&](const float4* cur, float4* out, int m, int r0, int r1, int rstep) {
+      const int nr = (r1 - r0 + rstep - 1) / rstep;
+      for (int t = threadIdx.x / kPNV; t < nr * npair; t += gstep) {
+        const int ri = t / npair;
+        const int r = r0 + ri * rstep, x = 2 * (t - ri * npair);
+        const float4* cqA = reinterpret_cast<const float4*>(coef + ((size_t)r * nx + x) * kCoef);
+        const float4* cqB = x + 1 < nx ? cqA + kCoef / 2 : cqA;  // odd nx: the last pair has one site
+        ulonglong2 oA0, oA1, oB0, oB1;
+        stencil_2site<kPNV>(row_below(cur, r) + v, cur + (size_t)r * rowsz + v, row_above(cur, r) + v, cqA, cqB, x,
+                            nx, oA0, oA1, oB0, oB1);
+        emit(out, m, r, x, oA0, oA1);
+        if (x + 1 < nx) emit(out, m, r, x + 1, oB0, oB1);
       }
     };
 
@@ -1556,13 +1625,10 @@ __global__ void __cluster_dims__(kPClu, 1, 1) __launch_bounds__(512, 1)
       const float4* cur = (m & 1) ? V1buf : V0buf;
       float4* out = (m & 1) ? V0buf : V1buf;
       fetch_halo(m & 1);
-      if (nrow > 2) rows(cur, out, m, 1, nrow - 1);  // interior rows while the halo arrives
+      if (nrow > 2) rows(cur, out, m, 1, nrow - 1, 1);  // interior rows while the halo arrives
       cp_wait_0();
       __syncthreads();
-      if (nrow > 0) {
-        rows(cur, out, m, 0, 1);
-        if (nrow > 1) rows(cur, out, m, nrow - 1, nrow);
-      }
+      if (nrow > 0) rows(cur, out, m, 0, nrow, nrow > 1 ? nrow - 1 : 1);  // rows 0 and nrow - 1
       if (m >= 1) sums(cur, m);
       cluster.sync();
     }
@@ -1769,7 +1835,30 @@ cudaError_t launch_f64(const ChebPlan& p, const void* table, const void* Vcur, c
 
 }  // namespace
 
-ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request) {
+// Wave model of a one-step launch: chunks x nb CTAs (nb bands of ceil(ny/nb)
+// rows) run one per SM (512 threads at 128 registers) in ceil(CTAs / SMs)
+// waves; a CTA costs its rows plus two halo rows of V_m (one of the three
+// vectors a row streams).  Returns the band heights of the cheapest choices.
+int band_rows_candidates(int ny, int64_t chunks, int* out, int maxn) {
+  std::vector<std::pair<double, int>> cost;
+  int last = -1;
+  for (int nb = 1; nb <= ny; ++nb) {
+    const int rows = (ny + nb - 1) / nb;
+    if (rows == last) continue;
+    last = rows;
+    const int bands = (ny + rows - 1) / rows;
+    const int64_t waves = (chunks * bands + kSMs - 1) / kSMs;
+    cost.push_back({(double)waves * (rows + 2.0 / 3.0), rows});
+  }
+  std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first < b.first;
+  });
+  int n = 0;
+  for (size_t k = 0; k < cost.size() && n < maxn; ++k) out[n++] = cost[k].second;
+  return n;
+}
+
+ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request, int band_rows) {
   ChebPlan p;
   p.nx = nx;
   p.ny = ny;
@@ -1827,7 +1916,7 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request)
   const int64_t chunks = p.ldv / p.cb;
   const int64_t want = 4 * kSMs;
   const int yblocks = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
-  p.ylen = std::max(1, (ny + yblocks - 1) / yblocks);
+  p.ylen = band_rows > 0 ? std::min(band_rows, ny) : std::max(1, (ny + yblocks - 1) / yblocks);
   if (precision == KPM_FP32) {
     // double step: widest chunk (<= cb) whose three rings fit; bands of at
     // least 4 rows (each band recomputes two halo rows of V_{m+1} and reads

@@ -108,8 +108,9 @@ struct kpm_ctx {
   int p_launched = 0;              // 1 when the captured batch graph holds the persistent launch
   double p_bytes = 0;              // its streaming-equivalent bytes per iteration
 
-  // autotuned (block_width, cols_per_block, double-step flag) per (nx, ny, precision, half pass, probe_p)
-  std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> tuned;
+  // autotuned (block_width, cols_per_block, double-step flag, band_rows) per (nx, ny, precision, half pass,
+  // probe_p, M)
+  std::map<std::tuple<int, int, int, int, int, int>, std::tuple<int, int, int, int>> tuned;
 
   // cached iteration graph
   cudaGraphExec_t graph = nullptr;
@@ -230,6 +231,7 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64 && o->precision != KPM_DF64)
     return fail(ctx, KPM_EINVAL, "unknown precision");
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
+  if (o->band_rows < 0) return fail(ctx, KPM_EINVAL, "negative band_rows");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
   if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return fail(ctx, KPM_EINVAL, "temperature must be finite and >= 0");
@@ -263,7 +265,7 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
     const int64_t fit = (int64_t)(ctx->budget / ((want_dbl ? 4 : 2) * (uint64_t)D * pp->elem));
     width = balanced_width(ncols, std::min<int64_t>(width, std::max<int64_t>(fit, 1)));
   }
-  pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
+  pp->cheb = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block, o->band_rows);
   pp->cheb.js = js;
   pp->cheb.probe_p = pp_;
   pp->cheb.probe_seed = (uint32_t)o->probe_seed;
@@ -1171,7 +1173,7 @@ int rmft_iterate_batched(kpm_ctx* ctx, int ncell, const kpm_model* models, const
   for (size_t k = 0; k < members.size(); ++k) {
     const kpm_model& m0 = models[members[k][0]];
     const int64_t D = 2 * (int64_t)m0.nx * m0.ny;
-    plans[k] = plan_cheb(m0.nx, m0.ny, D, prec, opts->cols_per_block);
+    plans[k] = plan_cheb(m0.nx, m0.ny, D, prec, opts->cols_per_block, opts->band_rows);
     if (plans[k].cb == 0) return fail(ctx, KPM_EINVAL, "lattice row too wide for the shared-memory window");
     // spread one step over the whole batch: y bands so that every cell fills its share
     const int64_t chunks = plans[k].ldv / plans[k].cb;
@@ -1533,12 +1535,14 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   const int64_t D = 2 * (int64_t)N;
   const int prec = opts->precision;
   *best = *opts;
-  auto key = std::make_tuple(model->nx, model->ny, prec, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0, opts->probe_p);
+  auto key = std::make_tuple(model->nx, model->ny, prec, (opts->flags & KPM_FLAG_PH_HALF) ? 1 : 0, opts->probe_p,
+                             opts->M);
   auto hit = ctx->tuned.find(key);
   if (hit != ctx->tuned.end()) {
     best->block_width = std::get<0>(hit->second);
     best->cols_per_block = std::get<1>(hit->second);
     best->flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | std::get<2>(hit->second);
+    best->band_rows = std::get<3>(hit->second);
     if (best_ms_per_step) *best_ms_per_step = -1.0;
     return KPM_OK;
   }
@@ -1557,38 +1561,67 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
     if (bw < widths.back()) widths.push_back(bw);
   }
   std::vector<int> cols = prec == KPM_FP32 ? std::vector<int>{16, 8, 4} : std::vector<int>{8, 4, 2};
-  const int Mt = 32;  // trial order: init/gather amortised, well under a second per trial at 10^4 sites
-  double best_t = 1e300;
-  int best_w = 0, best_c = 0, best_f = 0;
+  // two trial orders: their difference is the per-moment time without the
+  // per-slab start and gather, and the line through both predicts the pass
+  // at the requested order (one wide slab has the least start/gather time, but
+  // not always the fastest steps)
+  const int Mt1 = 18, Mt2 = 34;
+  const double Mreq = (double)std::max(opts->M, 2);
+  double best_t = 1e300, best_step = 0.0;
+  int best_w = 0, best_c = 0, best_f = 0, best_b = 0;
   std::vector<int> modes = prec == KPM_FP32 ? std::vector<int>{0, KPM_FLAG_DOUBLE_STEP} : std::vector<int>{0};
   for (int64_t w : widths) {
     for (int c : cols) for (int mode : modes) {
       kpm_opts o = *opts;
-      o.M = Mt;
+      o.M = Mt2;
       o.site_begin = o.site_end = 0;
       o.block_width = (int)w;
       o.cols_per_block = c;
+      o.band_rows = 0;
       o.flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | mode;
       PassPlan pp;
       if (plan_pass(ctx, model, &o, &pp) != KPM_OK) continue;
       if (pp.cheb.cb != c) continue;  // chunk does not fit for this lattice
       if (mode && !pp.dbl) continue;  // no double-step plan for this lattice
-      if ((r = ensure_pass_scratch(ctx, model, &o, pp))) break;
-      // one warm-up pass, one timed
-      if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
-      KPM_CU(cudaEventRecord(e0, s));
-      if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
-      KPM_CU(cudaEventRecord(e1, s));
-      KPM_CU(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      KPM_CU(cudaEventElapsedTime(&ms, e0, e1));
-      const double per_step = ms / (Mt - 1);
-      if (per_step < best_t) {
-        best_t = per_step;
-        best_w = o.block_width;
-        best_c = c;
-        best_f = mode;
+      // band heights of the one-step kernels: the default and the two best of
+      // the wave model (the double-step kernel keeps its own bands)
+      int bands[3] = {0, 0, 0};
+      int nband = 1;
+      if (!mode) {
+        int cand[2];
+        const int nc = band_rows_candidates(model->ny, pp.cheb.ldv / pp.cheb.cb, cand, 2);
+        for (int k = 0; k < nc; ++k)
+          if (cand[k] != pp.cheb.ylen) bands[nband++] = cand[k];
       }
+      for (int bk = 0; bk < nband && !r; ++bk) {
+        o.band_rows = bands[bk];
+        o.M = Mt2;
+        if (bk && plan_pass(ctx, model, &o, &pp) != KPM_OK) continue;
+        if ((r = ensure_pass_scratch(ctx, model, &o, pp))) break;
+        // one warm-up pass, then one timed pass at each trial order
+        if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
+        float ms[2] = {0.f, 0.f};
+        for (int k = 0; k < 2 && !r; ++k) {
+          o.M = k ? Mt2 : Mt1;
+          KPM_CU(cudaEventRecord(e0, s));
+          if ((r = enqueue_pass(ctx, model, &o, pp, fields, ab, ctx->obs, nullptr, s))) break;
+          KPM_CU(cudaEventRecord(e1, s));
+          KPM_CU(cudaEventSynchronize(e1));
+          KPM_CU(cudaEventElapsedTime(&ms[k], e0, e1));
+        }
+        if (r) break;
+        const double per_step = std::max(0.0, (double)(ms[1] - ms[0]) / (Mt2 - Mt1));
+        const double predicted = ms[0] + per_step * (Mreq - Mt1);
+        if (predicted < best_t) {
+          best_t = predicted;
+          best_step = per_step;
+          best_w = o.block_width;
+          best_c = c;
+          best_f = mode;
+          best_b = o.band_rows;
+        }
+      }
+      if (r) break;
     }
     if (r) break;
   }
@@ -1596,11 +1629,12 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
   cudaEventDestroy(e1);
   if (r) return r;
   if (best_c == 0) return fail(ctx, KPM_EINVAL, "no recursion configuration fits this lattice");
-  ctx->tuned[key] = std::make_tuple(best_w, best_c, best_f);
+  ctx->tuned[key] = std::make_tuple(best_w, best_c, best_f, best_b);
   best->block_width = best_w;
+  best->band_rows = best_b;
   best->cols_per_block = best_c;
   best->flags = (opts->flags & ~KPM_FLAG_DOUBLE_STEP) | best_f;
-  if (best_ms_per_step) *best_ms_per_step = best_t;
+  if (best_ms_per_step) *best_ms_per_step = best_step;
   return KPM_OK;
 }
 

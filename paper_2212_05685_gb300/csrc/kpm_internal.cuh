@@ -117,7 +117,10 @@ cudaError_t launch_update(int N, double* params, double* obs, double* mu_eff, co
 int reduce_scratch_doubles(int64_t n);
 
 // ---------------------------------------------------------------- cheb_kernels.cu
-ChebPlan plan_cheb(int nx, int ny, int64_t ldv_cols, int precision, int cb_request);
+ChebPlan plan_cheb(int nx, int ny, int64_t ldv_cols, int precision, int cb_request, int band_rows = 0);
+// up to maxn band heights (lattice rows per CTA) for chunks column chunks of
+// an ny-row lattice, best first by a wave model of the one-step kernels
+int band_rows_candidates(int ny, int64_t chunks, int* out, int maxn);
 // bytes of the per-site 2h~ table (kCoef complex entries)
 size_t table_bytes_per_site(int precision);
 cudaError_t cheb_prepare(const ChebPlan& p, int precision);

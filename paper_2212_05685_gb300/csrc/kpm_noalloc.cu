@@ -80,7 +80,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
   if ((o->flags & KPM_FLAG_PH_HALF) || o->probe_p) return KPM_EINVAL;  // the exact full pass only
-  if (o->block_width < 0 || o->cols_per_block < 0) return KPM_EINVAL;
+  if (o->block_width < 0 || o->cols_per_block < 0 || o->band_rows < 0) return KPM_EINVAL;
   if (o->site_begin != 0 || o->site_end != 0) return KPM_EINVAL;      // all sites
   if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return KPM_EINVAL;
   int dev = 0;
@@ -110,7 +110,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   ChebPlan p;
   p.cb = 0;
   while (width >= 1) {
-    p = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block);
+    p = plan_cheb(m->nx, m->ny, width, o->precision, o->cols_per_block, o->band_rows);
     if (p.cb == 0) return KPM_EINVAL;
     if (2 * (size_t)D * p.ldv * elem + 2 * 255 <= avail) break;
     width -= p.cb;

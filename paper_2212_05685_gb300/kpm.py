@@ -41,7 +41,7 @@ class kpm_opts(ctypes.Structure):
                 ("cols_per_block", ctypes.c_int32), ("margin", ctypes.c_double), ("temperature", ctypes.c_double),
                 ("flags", ctypes.c_int32),
                 ("probe_p", ctypes.c_int32), ("probe_seed", ctypes.c_int32), ("site_begin", ctypes.c_int32),
-                ("site_end", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("site_end", ctypes.c_int32), ("band_rows", ctypes.c_int32)]
 
 
 class kpm_rmft_opts(ctypes.Structure):
@@ -147,9 +147,9 @@ def make_model(nx, ny, t=1.0, tp=-0.3, J=0.3, flux=1, gutzwiller=True):
 
 
 def make_opts(M, precision=KPM_FP32, block_width=0, cols_per_block=0, margin=0.01, flags=0, probe_p=0,
-              probe_seed=0, temperature=0.0, site_begin=0, site_end=0):
+              probe_seed=0, temperature=0.0, site_begin=0, site_end=0, band_rows=0):
     return kpm_opts(M, precision, block_width, cols_per_block, margin, temperature, flags, probe_p, probe_seed,
-                    site_begin, site_end, 0)
+                    site_begin, site_end, band_rows)
 
 
 def make_rmft_opts(n_target, alpha=0.5, alpha_n=0.05, eta=0.5, tol=1e-7, paramagnetic=True, strict=False,

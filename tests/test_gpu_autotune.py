@@ -29,7 +29,7 @@ def test_autotune_choice_is_valid_and_cached(nx, ny, prec):
     M = 128
     base = kpm.make_opts(M, prec)
     best, ms = kpm.kpm_autotune(ctx, model, base, fields, ab)
-    assert ms > 0.0
+    assert ms >= 0.0  # time per moment from the difference of two trial passes
     assert 1 <= best.block_width <= 2 * N
     assert best.cols_per_block in ((16, 8, 4) if prec == 1 else (8, 4, 2))
     assert best.M == M and best.precision == prec
