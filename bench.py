@@ -1078,7 +1078,10 @@ def profile_batched():
 
 def profile_small(double_step=False):
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
-    (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per slab."""
+    (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per
+    slab, in bands of 34 lattice rows (the band height the autotuner picks for
+    the benchmark's 20000-column slab, so that a launch reads the same halo
+    rows per column)."""
     import torch
     from paper_2212_05685_gb300 import build, inputs, kpm
     build.build()
@@ -1094,7 +1097,7 @@ def profile_small(double_step=False):
     obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
     kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
     kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
-    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000,
+    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000, band_rows=34,
                                                   flags=kpm.KPM_FLAG_DOUBLE_STEP if double_step else 0), fields, ab, obs)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(obs).all())

@@ -106,7 +106,9 @@ typedef struct {
                            from those columns); with probing, KPM_EINVAL. */
   int32_t band_rows;    /* lattice rows per CTA of the one-step recursion kernels (each
                            CTA runs a band of rows of one column chunk); 0 = the
-                           library's choice, else min(band_rows, ny).  Changes the
+                           library's choice (the best of a wave model: chunks x
+                           bands CTAs, one per SM, each costing its rows plus
+                           two halo rows of one vector), else min(band_rows, ny).  Changes the
                            launch shape only, not the result; kpm_autotune searches
                            it.  Negative: KPM_EINVAL. */
 } kpm_opts;
@@ -289,8 +291,9 @@ int rmft_update(kpm_ctx* ctx, const kpm_model* model, const kpm_rmft_opts* ropts
  * for every slab width in {D, 8192, ..., 128} (narrow slabs keep both
  * recursion vectors in L2), every column chunk that fits shared memory and
  * (FP32) one or two steps per launch, and for one step per launch the
- * default band height and the two best of a wave model of the launch (CTAs
- * of ceil(ny / bands) rows, one per SM), predicts the pass at opts->M from the
+ * three best band heights of a wave model of the launch (CTAs of
+ * ceil(ny / bands) rows, one per SM; the first is the default of band_rows
+ * = 0) and one band per column chunk, predicts the pass at opts->M from the
  * line through both times (per-slab start and gather plus M - 1 steps), and
  * writes the fastest (block_width, cols_per_block, band_rows,
  * KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields copied from

@@ -452,16 +452,6 @@ __device__ __forceinline__ int nambu_slot(int x, int al) {
   return SW ? (al ^ (x & 1)) : al;
 }
 
-// Order of the terms of one output row: the nine stencil positions row by
-// row (lattice row y-1, y, y+1; x-1, x, x+1 in each), at each neighbour its
-// hopping entry and, for the four nearest neighbours, its pairing entry.  Every
-// FP32 kernel accumulates in this order, so all of them (one or two steps per
-// launch, streaming or persistent, one or two sites per thread) give the same
-// bits.  Position p = 3 (dy + 1) + (dx + 1) -> neighbour index k of the table
-// entries (1 + k, 9 + k hopping; 17 + k, 21 + k pairing for k < 4), -1 = the
-// site itself (the real diagonals, entry 0)
-__device__ constexpr int kPosK[9] = {5, 3, 6, 1, -1, 0, 7, 2, 4};
-
 template <int NV, bool SW = false>
 __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0, const float4* wp,
                                              const float2* cf_row, int x, int nx, ulonglong2& o0, ulonglong2& o1) {
@@ -472,28 +462,27 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
 #define KPM_L(W, XX, AL) \
   (*reinterpret_cast<const ulonglong2*>((W) + (XX) * RS + nambu_slot<NV, SW>((XX), (AL)) * NV))
   Acc2 a0 = {0ull, 0ull, 0ull, 0ull}, a1 = {0ull, 0ull, 0ull, 0ull};
-  const float4* wr[3] = {wm, w0, wp};
-  const int xs[3] = {xl, x, xr};
+  {
+    const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
+    const ulonglong2 u0 = KPM_L(w0, x, 0), u1 = KPM_L(w0, x, 1);
+    const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+    a0.pr = f2fma(d0, u0.x, a0.pr);
+    a0.pi = f2fma(d0, u0.y, a0.pi);
+    a1.pr = f2fma(d1, u1.x, a1.pr);
+    a1.pi = f2fma(d1, u1.y, a1.pi);
+  }
+  // neighbours k = 1..8: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1)
+  const float4* wk[8] = {w0, w0, wp, wm, wp, wm, wm, wp};
+  const int xk[8] = {xr, xl, x, x, xr, xl, xr, xl};
 #pragma unroll
-  for (int pos = 0; pos < 9; ++pos) {
-    const int k = kPosK[pos];
-    const float4* W = wr[pos / 3];
-    const int xx = xs[pos % 3];
-    const ulonglong2 u0 = KPM_L(W, xx, 0), u1 = KPM_L(W, xx, 1);
-    if (k < 0) {
-      const float2 d = cf[0];  // (d0, d1): real diagonals of the two Nambu rows
-      const u64 d0 = dup2(d.x), d1 = dup2(d.y);
-      a0.pr = f2fma(d0, u0.x, a0.pr);
-      a0.pi = f2fma(d0, u0.y, a0.pi);
-      a1.pr = f2fma(d1, u1.x, a1.pr);
-      a1.pi = f2fma(d1, u1.y, a1.pi);
-    } else {
-      acc_term(a0, cf[1 + k], u0);
-      acc_term(a1, cf[9 + k], u1);
-      if (k < 4) {
-        acc_term(a0, cf[17 + k], u1);
-        acc_term(a1, cf[21 + k], u0);
-      }
+  for (int k = 0; k < 8; ++k) {
+    const ulonglong2 u0 = KPM_L(wk[k], xk[k], 0);
+    const ulonglong2 u1 = KPM_L(wk[k], xk[k], 1);
+    acc_term(a0, cf[1 + k], u0);
+    acc_term(a1, cf[9 + k], u1);
+    if (k < 4) {
+      acc_term(a0, cf[17 + k], u1);
+      acc_term(a1, cf[21 + k], u0);
     }
   }
 #undef KPM_L
@@ -501,88 +490,110 @@ __device__ __forceinline__ void stencil_site(const float4* wm, const float4* w0,
   o1 = make_ulonglong2(f2sub(a1.pr, a1.qi), f2add(a1.pi, a1.qr));
 }
 
-// The persistent kernel keeps a site's entries in the order the terms use
-// them: kCoefOrder[i] = table entry at stored position i (entry 0 holds both
-// real diagonals; the last position is padding)
-__constant__ int kCoefOrder[kCoef] = {6,  14, 4,  12, 20, 24, 7,  15,         // row y-1
-                                      2,  10, 18, 22, 0,  1,  9,  17, 21,     // row y
-                                      8,  16, 3,  11, 19, 23, 5,  13, 25};    // row y+1
+// The persistent kernel keeps a site's entries in the order stencil_site
+// uses them: kCoefOrder[i] = table entry at stored position i (the real
+// diagonals, then per neighbour k = 0..7 its hopping entries and, for k < 4,
+// its pairing entries; the last position is padding)
+__constant__ int kCoefOrder[kCoef] = {0, 1, 9,  17, 21, 2, 10, 18, 22, 3,  11, 19, 23,
+                                      4, 12, 20, 24, 5, 13, 6,  14, 7,  15, 8,  16, 25};
 
 // Two neighbouring sites x and x + 1 of one lattice row for one column pair
-// (both Nambu rows each), the same terms in the same order as stencil_site:
-// the four V_m positions x-1 .. x+2 of each row are loaded once for both
-// sites (24 instead of 36 loads).  cqA, cqB: the two sites' entries in
-// kCoefOrder order as 16-byte pairs.
+// (both Nambu rows each), every term in the order of stencil_site (so the
+// bits are the same): the twelve V_m positions x-1 .. x+2 of rows y-1, y, y+1
+// are loaded once for both sites (24 instead of 36 loads), site B's term k
+// following site A's, each position dropped after its last use.  cqA, cqB:
+// the sites' entries in kCoefOrder order as 16-byte pairs.
 template <int NV>
 __device__ __forceinline__ void stencil_2site(const float4* wm, const float4* w0, const float4* wp,
                                               const float4* cqA, const float4* cqB, int x, int nx,
                                               ulonglong2& oA0, ulonglong2& oA1, ulonglong2& oB0, ulonglong2& oB1) {
   constexpr int RS = 2 * NV;
-  // x-1, x, x+1, x+2 (periodic)
-  int xs[4];
-  xs[0] = x == 0 ? nx - 1 : x - 1;
-  xs[1] = x;
-  xs[2] = x + 1 >= nx ? x + 1 - nx : x + 1;
-  xs[3] = x + 2 >= nx ? x + 2 - nx : x + 2;
-  Acc2 A0 = {0ull, 0ull, 0ull, 0ull}, A1 = {0ull, 0ull, 0ull, 0ull};
-  Acc2 B0 = {0ull, 0ull, 0ull, 0ull}, B1 = {0ull, 0ull, 0ull, 0ull};
-  const float4* wr[3] = {wm, w0, wp};
-  float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
-  // stored entry i of a site: half (i & 1) of pair i >> 1, loaded when first needed
-  auto ent = [](const float4& q, int i) { return (i & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y); };
-  // one term of site S (0 = A, 1 = B) at stored position i
-  auto term = [&](Acc2& a, int S, int i, ulonglong2 u) {
-    if ((i & 1) == 0) {
-      if (S == 0) qa = cqA[i >> 1]; else qb = cqB[i >> 1];
-    }
-    acc_term(a, ent(S == 0 ? qa : qb, i), u);
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int x1 = x + 1 >= nx ? x + 1 - nx : x + 1;
+  const int x2 = x + 2 >= nx ? x + 2 - nx : x + 2;
+  struct Site {
+    Acc2 a0, a1;
+    float4 q;
+    const float4* cq;
   };
-  // stored position of the first entry of stencil position pos (row-major)
-  constexpr int kFirst[9] = {0, 2, 6, 8, 12, 13, 17, 19, 23};
-#pragma unroll
-  for (int row = 0; row < 3; ++row) {
-    const float4* W = wr[row];
-    ulonglong2 u[4][2];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      u[j][0] = *reinterpret_cast<const ulonglong2*>(W + xs[j] * RS);
-      u[j][1] = *reinterpret_cast<const ulonglong2*>(W + xs[j] * RS + NV);
+  Site A = {{0ull, 0ull, 0ull, 0ull}, {0ull, 0ull, 0ull, 0ull}, make_float4(0.f, 0.f, 0.f, 0.f), cqA};
+  Site B = {{0ull, 0ull, 0ull, 0ull}, {0ull, 0ull, 0ull, 0ull}, make_float4(0.f, 0.f, 0.f, 0.f), cqB};
+  struct U {
+    ulonglong2 e, h;  // Nambu slots 0 and 1 of one position
+  };
+  auto ld = [&](const float4* W, int xx) {
+    U u;
+    u.e = *reinterpret_cast<const ulonglong2*>(W + xx * RS);
+    u.h = *reinterpret_cast<const ulonglong2*>(W + xx * RS + NV);
+    return u;
+  };
+  // stored entry i of a site, its 16-byte pair loaded when first needed (even i)
+  auto cf = [](Site& S, int i) {
+    if ((i & 1) == 0) S.q = S.cq[i >> 1];
+    return (i & 1) ? make_float2(S.q.z, S.q.w) : make_float2(S.q.x, S.q.y);
+  };
+  auto diag = [&](Site& S, const U& u) {
+    const float2 d = cf(S, 0);
+    const u64 d0 = dup2(d.x), d1 = dup2(d.y);
+    S.a0.pr = f2fma(d0, u.e.x, S.a0.pr);
+    S.a0.pi = f2fma(d0, u.e.y, S.a0.pi);
+    S.a1.pr = f2fma(d1, u.h.x, S.a1.pr);
+    S.a1.pi = f2fma(d1, u.h.y, S.a1.pi);
+  };
+  // neighbour k: stored positions 1 + 4k (k < 4, with pairing) or 17 + 2 (k - 4)
+  auto nb = [&](Site& S, int k, const U& u) {
+    const int i = k < 4 ? 1 + 4 * k : 17 + 2 * (k - 4);
+    acc_term(S.a0, cf(S, i), u.e);
+    acc_term(S.a1, cf(S, i + 1), u.h);
+    if (k < 4) {
+      acc_term(S.a0, cf(S, i + 2), u.h);
+      acc_term(S.a1, cf(S, i + 3), u.e);
     }
-#pragma unroll
-    for (int S = 0; S < 2; ++S) {
-      Acc2& a0 = S == 0 ? A0 : B0;
-      Acc2& a1 = S == 0 ? A1 : B1;
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const int pos = 3 * row + dx;
-        const int k = kPosK[pos];
-        const ulonglong2 u0 = u[S + dx][0], u1 = u[S + dx][1];
-        const int i = kFirst[pos];
-        if (k < 0) {
-          if ((i & 1) == 0) {
-            if (S == 0) qa = cqA[i >> 1]; else qb = cqB[i >> 1];
-          }
-          const float2 d = ent(S == 0 ? qa : qb, i);
-          const u64 d0 = dup2(d.x), d1 = dup2(d.y);
-          a0.pr = f2fma(d0, u0.x, a0.pr);
-          a0.pi = f2fma(d0, u0.y, a0.pi);
-          a1.pr = f2fma(d1, u1.x, a1.pr);
-          a1.pi = f2fma(d1, u1.y, a1.pi);
-        } else {
-          term(a0, S, i, u0);
-          term(a1, S, i + 1, u1);
-          if (k < 4) {
-            term(a0, S, i + 2, u1);
-            term(a1, S, i + 3, u0);
-          }
-        }
-      }
-    }
+  };
+  // k: (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1), as in stencil_site
+  const U c0 = ld(w0, x), c1 = ld(w0, x1);
+  diag(A, c0);
+  diag(B, c1);
+  {
+    const U c2 = ld(w0, x2);
+    nb(A, 0, c1);
+    nb(B, 0, c2);
   }
-  oA0 = make_ulonglong2(f2sub(A0.pr, A0.qi), f2add(A0.pi, A0.qr));
-  oA1 = make_ulonglong2(f2sub(A1.pr, A1.qi), f2add(A1.pi, A1.qr));
-  oB0 = make_ulonglong2(f2sub(B0.pr, B0.qi), f2add(B0.pi, B0.qr));
-  oB1 = make_ulonglong2(f2sub(B1.pr, B1.qi), f2add(B1.pi, B1.qr));
+  {
+    const U cm = ld(w0, xm);
+    nb(A, 1, cm);
+    nb(B, 1, c0);
+  }
+  const U p0 = ld(wp, x), p1 = ld(wp, x1);
+  nb(A, 2, p0);
+  nb(B, 2, p1);
+  const U m0 = ld(wm, x), m1 = ld(wm, x1);
+  nb(A, 3, m0);
+  nb(B, 3, m1);
+  {
+    const U p2 = ld(wp, x2);
+    nb(A, 4, p1);
+    nb(B, 4, p2);
+  }
+  {
+    const U mm = ld(wm, xm);
+    nb(A, 5, mm);
+    nb(B, 5, m0);
+  }
+  {
+    const U m2 = ld(wm, x2);
+    nb(A, 6, m1);
+    nb(B, 6, m2);
+  }
+  {
+    const U pm = ld(wp, xm);
+    nb(A, 7, pm);
+    nb(B, 7, p0);
+  }
+  oA0 = make_ulonglong2(f2sub(A.a0.pr, A.a0.qi), f2add(A.a0.pi, A.a0.qr));
+  oA1 = make_ulonglong2(f2sub(A.a1.pr, A.a1.qi), f2add(A.a1.pi, A.a1.qr));
+  oB0 = make_ulonglong2(f2sub(B.a0.pr, B.a0.qi), f2add(B.a0.pi, B.a0.qr));
+  oB1 = make_ulonglong2(f2sub(B.a1.pr, B.a1.qi), f2add(B.a1.pi, B.a1.qr));
 }
 
 // moment sums acc[J][s] += a V[K_s(J), J] for the columns of the chunk whose
@@ -1911,12 +1922,12 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request,
   p.rec = nullptr;
   if (p.cb == 0) return p;
   p.ldv = (width + p.cb - 1) / p.cb * p.cb;
-  // enough CTAs to fill the GPU a few times over: split y only when the
-  // column chunks alone do not
+  // band height of the one-step kernels: the caller's, else the best of the
+  // wave model (the last wave of a launch as full as the halo rows allow)
   const int64_t chunks = p.ldv / p.cb;
-  const int64_t want = 4 * kSMs;
-  const int yblocks = (int)std::min<int64_t>(ny, std::max<int64_t>(1, (want + chunks - 1) / chunks));
-  p.ylen = band_rows > 0 ? std::min(band_rows, ny) : std::max(1, (ny + yblocks - 1) / yblocks);
+  int best_rows = ny;
+  band_rows_candidates(ny, chunks, &best_rows, 1);
+  p.ylen = band_rows > 0 ? std::min(band_rows, ny) : best_rows;
   if (precision == KPM_FP32) {
     // double step: widest chunk (<= cb) whose three rings fit; bands of at
     // least 4 rows (each band recomputes two halo rows of V_{m+1} and reads

@@ -1583,15 +1583,20 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
       if (plan_pass(ctx, model, &o, &pp) != KPM_OK) continue;
       if (pp.cheb.cb != c) continue;  // chunk does not fit for this lattice
       if (mode && !pp.dbl) continue;  // no double-step plan for this lattice
-      // band heights of the one-step kernels: the default and the two best of
-      // the wave model (the double-step kernel keeps its own bands)
-      int bands[3] = {0, 0, 0};
+      // band heights of the one-step kernels: the default (the wave model's
+      // best), its next two, and one band per chunk (the double-step kernel
+      // keeps its own bands)
+      int bands[4] = {0, 0, 0, 0};
       int nband = 1;
       if (!mode) {
-        int cand[2];
-        const int nc = band_rows_candidates(model->ny, pp.cheb.ldv / pp.cheb.cb, cand, 2);
-        for (int k = 0; k < nc; ++k)
-          if (cand[k] != pp.cheb.ylen) bands[nband++] = cand[k];
+        int cand[4];
+        int nc = band_rows_candidates(model->ny, pp.cheb.ldv / pp.cheb.cb, cand, 3);
+        cand[nc++] = model->ny;
+        for (int k = 0; k < nc; ++k) {
+          bool seen = cand[k] == pp.cheb.ylen;
+          for (int j = 1; j < nband; ++j) seen = seen || bands[j] == cand[k];
+          if (!seen) bands[nband++] = cand[k];
+        }
       }
       for (int bk = 0; bk < nband && !r; ++bk) {
         o.band_rows = bands[bk];
