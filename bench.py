@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--block-width", type=int, default=0)
     ap.add_argument("--cols", type=int, default=0)
+    ap.add_argument("--band-rows", type=int, default=0,
+                    help="lattice rows per CTA of the one-step recursion (0: the library's choice)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -288,7 +290,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = kpm.kpm_create(local)
     model = kpm.make_model(w.nx, w.ny, w.t, w.tp, w.J, w.flux)
-    opts = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols,
+    opts = kpm.make_opts(M, kpm.KPM_FP32, args.block_width, args.cols, band_rows=args.band_rows,
                          flags=kpm.KPM_FLAG_DOUBLE_STEP if args.double_step else 0)
     ropts = kpm.make_rmft_opts(w.n_target, tol=0.0)
     phi = torch.empty(4 * N, dtype=torch.float64, device="cuda")
@@ -300,7 +302,7 @@ def run_ours(args):
     # recursion launch configuration: the library's autotuner (slab width,
     # column chunk) on this cell's Hamiltonian, unless fixed on the command line
     tune = None
-    if not args.no_autotune and args.block_width == 0 and args.cols == 0:
+    if not args.no_autotune and args.block_width == 0 and args.cols == 0 and args.band_rows == 0:
         f0 = torch.empty(26 * N, dtype=torch.float64, device="cuda")
         ab0 = torch.empty(2, dtype=torch.float64, device="cuda")
         kpm.kpm_build_H(ctx, model, phi, params, 0.0, f0)
@@ -1106,13 +1108,14 @@ def profile_small(double_step=False):
     return 0
 
 
-def width_study(half_width=0):
+def width_study(half_width=0, band_rows=0):
     """Per-step rate of the FP32 recursion on the benchmark lattice against the
     slab width, for the full pass and the particle-hole half pass: each
     configuration runs two passes of different order (M = 66 and 194), so the
     difference is the time of 128 steps per slab without the per-slab start
     and gather.  With half_width > 0, one half pass at that width and M = 8
-    (for ncu) instead."""
+    (for ncu, bands of band_rows lattice rows, 0 = the library's choice)
+    instead."""
     import torch
     from paper_2212_05685_gb300 import build, inputs, kpm
     build.build()
@@ -1130,8 +1133,8 @@ def width_study(half_width=0):
     kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
     ab[1] = 0.0  # the half pass needs the centre at 0; the full pass takes it too
     if half_width:
-        kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, half_width, 16, flags=kpm.KPM_FLAG_PH_HALF),
-                            fields, ab, obs)
+        kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, half_width, 16, flags=kpm.KPM_FLAG_PH_HALF,
+                                                      band_rows=band_rows), fields, ab, obs)
         torch.cuda.synchronize()
         assert bool(torch.isfinite(obs).all())
         kpm.kpm_destroy(ctx)
@@ -1200,7 +1203,7 @@ def main():
     if args.batched_study:
         return batched_study()
     if args.width_study is not None:
-        return width_study(args.width_study)
+        return width_study(args.width_study, args.band_rows)
     if args.profile_small:
         return profile_small(args.double_step)
     if args.profile_batched:
