@@ -73,6 +73,8 @@ def parse():
                     help="48x24 cell to self-consistency at 1e-7 (solve.converge) against linear mixing alone, and exit")
     ap.add_argument("--profile-batched", action="store_true",
                     help="one batched iteration (4 cells 48x24 and 2 cells 64x32, M=64, FP32) for ncu captures")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "df64"], default="fp32",
+                    help="recursion of --profile-small")
     ap.add_argument("--profile-small", action="store_true",
                     help="one FP32 pass on the 100x100 cell with 2000-column slabs and M=8, for ncu captures")
     ap.add_argument("--batched-study", action="store_true",
@@ -1078,12 +1080,13 @@ def profile_batched():
     return 0
 
 
-def profile_small(double_step=False):
+def profile_small(double_step=False, precision="fp32"):
     """Small case for ncu: the benchmark lattice, slabs of 2000 columns
     (2 x 320 MB, larger than L2), M = 8: seven recursion-step launches per
     slab, in bands of 34 lattice rows (the band height the autotuner picks for
     the benchmark's 20000-column slab, so that a launch reads the same halo
-    rows per column)."""
+    rows per column).  precision fp64 / df64: the same slabs through the FP64
+    or the double-float recursion."""
     import torch
     from paper_2212_05685_gb300 import build, inputs, kpm
     build.build()
@@ -1099,7 +1102,8 @@ def profile_small(double_step=False):
     obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
     kpm.kpm_build_H(ctx, model, phi, params, 0.0, fields)
     kpm.kpm_bounds(ctx, model, fields, 0.01, ab)
-    kpm.kpm_observables(ctx, model, kpm.make_opts(8, kpm.KPM_FP32, 2000, band_rows=34,
+    prec = {"fp32": kpm.KPM_FP32, "fp64": kpm.KPM_FP64, "df64": kpm.KPM_DF64}[precision]
+    kpm.kpm_observables(ctx, model, kpm.make_opts(8, prec, 2000, band_rows=34,
                                                   flags=kpm.KPM_FLAG_DOUBLE_STEP if double_step else 0), fields, ab, obs)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(obs).all())
@@ -1161,9 +1165,9 @@ def width_study(half_width=0, band_rows=0):
     for half, ncols, widths in ((0, D, (20000, 10000, 4000, 2000)), (1, D // 2, (10000, 5000, 2500))):
         for width in widths:
             configs.append((half, 0, ncols, width, kpm.KPM_FLAG_DOUBLE_STEP, 0))
-            for band in (0, 10, 20, 25, 34, 50, 100):
+            for band in (0, kpm.KPM_BAND_FLAT, 10, 20, 25, 34, 50, 100):
                 configs.append((half, 0, ncols, width, 0, band))
-    for band in (0, 2, 3, 4, 5, 7, 9, 10, 12):
+    for band in (0, kpm.KPM_BAND_FLAT, 3, 5, 9, 10, 12):
         configs.append((0, 10, 2 * 10 * 10, 2 * 10 * 10, 0, band))
     for half, probe, ncols, width, dbl, band in configs:
         flags = dbl | (kpm.KPM_FLAG_PH_HALF if half else 0)
@@ -1180,7 +1184,8 @@ def width_study(half_width=0, band_rows=0):
                      "s_per_pass_M2048": nslab * (over + 2047 * step)})
     print(json.dumps({"study": "slab width and band height", "cell": "100x100", "cols_per_block": 16,
                       "M": [M1, M2], "bytes_per_step": "3 D ldv 8 (read V_m, V_m-1, write V_m+1)",
-                      "band_rows": "0 = library default", "rows": rows}), flush=True)
+                      "band_rows": "0 = library default, -1 = flat split (one CTA per SM)", "rows": rows}),
+          flush=True)
     kpm.kpm_destroy(ctx)
     return 0
 
@@ -1205,7 +1210,7 @@ def main():
     if args.width_study is not None:
         return width_study(args.width_study, args.band_rows)
     if args.profile_small:
-        return profile_small(args.double_step)
+        return profile_small(args.double_step, args.precision)
     if args.profile_batched:
         return profile_batched()
     if args.profile_probing:

@@ -137,6 +137,52 @@ def test_directional_finite_differences(K):
         assert float(np.dot(got, v)) == pytest.approx(fd, rel=1e-6)
 
 
+def test_density_loss_componentwise_finite_differences(K):
+    """The adjoint workload's loss L = sum_i (n_i - n_target,i)^2 (seeded
+    targets 1 - delta + 0.01 U(-1, 1)) on a 24 x 24 vortex cell: every one of
+    16 seeded field components of the regenerating FP64 and FP32 gradients
+    against central differences with h = 1e-6 of FP64 forward passes (a, b
+    fixed); FP64 within 1e-7 of the largest entry, FP32 within 2e-5."""
+    kpm, ctx = K
+    nx, ny, M = 24, 24, 256
+    w = inputs.Workload(nx, ny, 0.125, inputs.two_vortex(nx, ny), M, seed=1)
+    model, phi, params, fields, ab = _prep(K, nx, ny, inputs.vortex_seed(w), mu=0.0)
+    N = nx * ny
+    nt = dev(inputs.target_density(w, seed=1))
+    obs = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+
+    def grad(prec):
+        kpm.kpm_observables(ctx, model, kpm.make_opts(M, prec, flags=kpm.KPM_FLAG_KEEP_TAIL), fields, ab, obs)
+        n = obs[:N] + obs[N:2 * N]
+        g = torch.zeros(26 * N, dtype=torch.float64, device="cuda")
+        g[:N] = 2 * (n - nt)
+        g[N:2 * N] = 2 * (n - nt)
+        out = torch.empty(26 * N, dtype=torch.float64, device="cuda")
+        kpm.kpm_backward(ctx, model, kpm.make_opts(M, prec), fields, ab, g, 0.0, out, ckpt_every=kpm.KPM_REGENERATE)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    g64, g32 = grad(kpm.KPM_FP64), grad(kpm.KPM_FP32)
+    o64 = kpm.make_opts(M, kpm.KPM_FP64)
+
+    def L(f):
+        kpm.kpm_observables(ctx, model, o64, f, ab, obs)
+        n = obs[:N] + obs[N:2 * N]
+        return float(((n - nt) ** 2).sum())
+
+    h = 1e-6
+    scale = float(np.abs(g64).max())
+    assert scale > 0.0
+    for k in np.random.default_rng(1).choice(26 * N, size=16, replace=False):
+        f = fields.clone()
+        f[int(k)] += h
+        lp = L(f)
+        f[int(k)] -= 2 * h
+        fd = (lp - L(f)) / (2 * h)
+        assert abs(g64[k] - fd) <= 1e-7 * scale, (int(k), g64[k], fd)
+        assert abs(g32[k] - fd) <= 2e-5 * scale, (int(k), g32[k], fd)
+
+
 def test_autograd_function(K):
     kpm, ctx = K
     from paper_2212_05685_gb300 import autograd
