@@ -1165,9 +1165,9 @@ def width_study(half_width=0, band_rows=0):
     for half, ncols, widths in ((0, D, (20000, 10000, 4000, 2000)), (1, D // 2, (10000, 5000, 2500))):
         for width in widths:
             configs.append((half, 0, ncols, width, kpm.KPM_FLAG_DOUBLE_STEP, 0))
-            for band in (0, kpm.KPM_BAND_FLAT, 10, 20, 25, 34, 50, 100):
+            for band in (0, 10, 20, 25, 34, 50, 100):
                 configs.append((half, 0, ncols, width, 0, band))
-    for band in (0, kpm.KPM_BAND_FLAT, 3, 5, 9, 10, 12):
+    for band in (0, 3, 5, 9, 10, 12):
         configs.append((0, 10, 2 * 10 * 10, 2 * 10 * 10, 0, band))
     for half, probe, ncols, width, dbl, band in configs:
         flags = dbl | (kpm.KPM_FLAG_PH_HALF if half else 0)
@@ -1184,8 +1184,7 @@ def width_study(half_width=0, band_rows=0):
                      "s_per_pass_M2048": nslab * (over + 2047 * step)})
     print(json.dumps({"study": "slab width and band height", "cell": "100x100", "cols_per_block": 16,
                       "M": [M1, M2], "bytes_per_step": "3 D ldv 8 (read V_m, V_m-1, write V_m+1)",
-                      "band_rows": "0 = library default, -1 = flat split (one CTA per SM)", "rows": rows}),
-          flush=True)
+                      "band_rows": "0 = library default", "rows": rows}), flush=True)
     kpm.kpm_destroy(ctx)
     return 0
 

@@ -105,18 +105,12 @@ typedef struct {
                            kpm_observables and kpm_backward (its gradient is then the part
                            from those columns); with probing, KPM_EINVAL. */
   int32_t band_rows;    /* lattice rows per CTA of the one-step recursion kernels (each
-                           CTA runs a band of rows of one column chunk), else
-                           min(band_rows, ny); KPM_BAND_FLAT: the FP32 TMA-staged
-                           step (chunks of 8 or 16 columns) runs one CTA per SM,
-                           each over an equal run of the chunks x ny chunk-rows
-                           taken chunk by chunk (other kernels: as 0); 0 = the
-                           library's choice: KPM_BAND_FLAT for that step when
-                           there are at least as many chunks as SMs, else the
-                           best of a wave model (chunks x bands CTAs, one per SM,
-                           each costing its rows plus two halo rows of one
-                           vector).  Changes the launch shape only, not the
-                           result; kpm_autotune searches it.  Other negative
-                           values: KPM_EINVAL. */
+                           CTA runs a band of rows of one column chunk); 0 = the
+                           library's choice (the best of a wave model: chunks x
+                           bands CTAs, one per SM, each costing its rows plus
+                           two halo rows of one vector), else min(band_rows, ny).  Changes the
+                           launch shape only, not the result; kpm_autotune searches
+                           it.  Negative: KPM_EINVAL. */
 } kpm_opts;
 
 /* kpm_opts.flags: run the FP32 recursion two steps per launch where the
@@ -140,8 +134,6 @@ typedef struct {
  * or FP64 unit-vector passes (KPM_EINVAL with probing, the half pass or
  * KPM_DF64); any kpm_observables call without the flag drops the tail. */
 #define KPM_FLAG_KEEP_TAIL 4
-/* kpm_opts.band_rows: the flat split of the FP32 TMA-staged step */
-#define KPM_BAND_FLAT (-1)
 
 /* kpm_backward ckpt_every: regenerate the forward vectors backwards instead
  * of checkpointing them (see kpm_backward) */
@@ -299,10 +291,9 @@ int rmft_update(kpm_ctx* ctx, const kpm_model* model, const kpm_rmft_opts* ropts
  * for every slab width in {D, 8192, ..., 128} (narrow slabs keep both
  * recursion vectors in L2), every column chunk that fits shared memory and
  * (FP32) one or two steps per launch, and for one step per launch the
- * default band_rows = 0, the flat split (KPM_BAND_FLAT, TMA-staged chunks),
- * the three best band heights of a wave model of the launch (CTAs of
- * ceil(ny / bands) rows, one per SM) and one band per column chunk, predicts
- * the pass at opts->M from the
+ * three best band heights of a wave model of the launch (CTAs of
+ * ceil(ny / bands) rows, one per SM; the first is the default of band_rows
+ * = 0) and one band per column chunk, predicts the pass at opts->M from the
  * line through both times (per-slab start and gather plus M - 1 steps), and
  * writes the fastest (block_width, cols_per_block, band_rows,
  * KPM_FLAG_DOUBLE_STEP bit of flags) into *best (other fields copied from

@@ -871,7 +871,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // skip a window copy; the production instantiation has neither
 template <int CB, int MODE, bool HOOK = false>
 __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx, int ny, int64_t D, int64_t ldv,
-                                                  int ylen, int brows, int flat, const float2* __restrict__ table,
+                                                  int ylen, int brows, const float2* __restrict__ table,
                                                   const float4* Vprev, float4* Vout, ColMap cmap,
                                                   double2* __restrict__ acc, const double* __restrict__ am,
                                                   const double* __restrict__ ao, int m) {
@@ -887,20 +887,11 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   const int rowsz = nx * RS;
   const int crow = nx * kCoef;
 
-  // The CTA's work: chunk-rows g = chunk ny + y in [g0, g1).  Banded (flat =
-  // 0): rows [bx ylen, bx ylen + ylen) of chunk by.  Flat: the chunks x ny
-  // chunk-rows split evenly over the grid (one CTA per SM), each CTA running
-  // its range as segments of consecutive rows of one chunk.
-  int64_t g0, g1;
-  if (flat) {
-    const int64_t tot = (ldv / CB) * ny;
-    g0 = (int64_t)blockIdx.x * tot / gridDim.x;
-    g1 = (int64_t)(blockIdx.x + 1) * tot / gridDim.x;
-  } else {
-    const int ya = blockIdx.x * ylen;
-    g0 = (int64_t)blockIdx.y * ny + ya;
-    g1 = (int64_t)blockIdx.y * ny + min(ny, ya + ylen);
-  }
+  const int64_t cb0 = (int64_t)blockIdx.y * CB;
+  const int64_t q0 = cb0 / 2;
+  const int y0 = blockIdx.x * ylen;
+  const int y1 = min(ny, y0 + ylen);
+  const int nrow = y1 - y0;
 
   const int v = threadIdx.x % NV;
   const int xs = threadIdx.x / NV;
@@ -923,26 +914,29 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   };
   int rot = 0;  // rotation of the CTA's current row
 
-  // the current segment: rows [y0, y1) of the chunk at column cb0
-  int64_t cb0 = 0, q0 = 0;
-  int y0 = 0, y1 = 0, nrow = 0;
   int yj_lo = ny, yj_hi = -1;
-  // ring positions continue from segment to segment: window row w of the
-  // segment is ring row wb + w (slot % 5), coefficient row c is cbs + c (% 3),
-  // computed row q is rb + q (row-done barrier % 3)
-  int wb = 0, cbs = 0, rb = 0;
+  {
+    const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
+    if (cmap.probe_p) {
+      yj_lo = 0;
+      yj_hi = ny - 1;
+    } else if (chi >= clo) {
+      yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
+      yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
+    }
+  }
 
   const uint32_t bar0 = smem_u32(bars);
   const uint32_t vbytes = (uint32_t)(2 * nx * CB * 8);  // one window row: 2 Nx Nambu rows x CB complex FP32
   const uint32_t cbytes = (uint32_t)(nx * kCoef * 8);   // one coefficient row
   const int nbox = 2 * nx / brows;
-  // window row w holds lattice row y0 - 1 + w (w = 0 .. nrow + 1), coefficient
-  // row c holds row y0 + c (c = 0 .. nrow - 1)
+  // window row w holds lattice row y0 - 1 + w (w = 0 .. nrow + 1) in slot w % 5,
+  // coefficient row c holds row y0 + c (c = 0 .. nrow - 1) in slot c % 3
   int w_hi = -1, c_hi = -1;  // last window / coefficient row issued (issuing thread)
   auto issue_v = [&](int w) {
     const int ly = wrapi(y0 - 1 + w, ny);
-    const uint32_t bar = bar0 + 8 * ((wb + w) % 5);
-    const uint32_t dst = smem_u32(win + ((wb + w) % 5) * rowsz);
+    const uint32_t bar = bar0 + 8 * (w % 5);
+    const uint32_t dst = smem_u32(win + (w % 5) * rowsz);
     if (HOOK && w == 2 && *reinterpret_cast<volatile int*>(&g_drop_copy) > 0 && atomicSub(&g_drop_copy, 1) > 0) {
       w_hi = w;  // skipped: the slot's phase never completes
       return;
@@ -953,34 +947,29 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     w_hi = w;
   };
   auto issue_c = [&](int c) {
-    const uint32_t bar = bar0 + 8 * (5 + (cbs + c) % 3);
+    const uint32_t bar = bar0 + 8 * (5 + c % 3);
     mbar_expect_tx(bar, cbytes);
-    bulk_load(smem_u32(coef + ((cbs + c) % 3) * crow), table + (int64_t)(y0 + c) * crow, cbytes, bar);
+    bulk_load(smem_u32(coef + (c % 3) * crow), table + (int64_t)(y0 + c) * crow, cbytes, bar);
     c_hi = c;
   };
-  auto vbar = [&](int w) { return bar0 + 8 * ((wb + w) % 5); };
-  auto vpar = [&](int w) { return (uint32_t)(((wb + w) / 5) & 1); };
-  auto cbar = [&](int c) { return bar0 + 8 * (5 + (cbs + c) % 3); };
-  auto cpar = [&](int c) { return (uint32_t)(((cbs + c) / 3) & 1); };
-  auto dbar = [&](int r) { return bar0 + 8 * (8 + (rb + r) % 3); };
-  auto dpar = [&](int r) { return (uint32_t)(((rb + r) / 3) & 1); };
+  auto vbar = [&](int w) { return bar0 + 8 * (w % 5); };
+  auto vpar = [&](int w) { return (uint32_t)((w / 5) & 1); };
+  auto cbar = [&](int c) { return bar0 + 8 * (5 + c % 3); };
+  auto cpar = [&](int c) { return (uint32_t)((c / 3) & 1); };
+  auto dbar = [&](int r) { return bar0 + 8 * (8 + r % 3); };
+  auto dpar = [&](int r) { return (uint32_t)((r / 3) & 1); };
 
-  // NaN over the output rows of chunk-rows [ga, g1) (after a failure)
-  auto poison = [&](int64_t ga) {
+  auto poison = [&]() {  // NaN over the CTA's output rows
     const float nan = __int_as_float(0x7fc00000);
     const float4 nan4 = make_float4(nan, nan, nan, nan);
-    const int per = 2 * nx * NV;  // float4 of one chunk-row
-    for (int64_t t = threadIdx.x; t < (g1 - ga) * per; t += blockDim.x) {
-      const int64_t g = ga + t / per;
-      const int k = (int)(t % per), r = k / NV, c = k - r * NV;
-      const int64_t ch = g / ny;
-      const int y = (int)(g - ch * ny);
-      Vout[((int64_t)2 * nx * y + r) * ldq + ch * NV + c] = nan4;
+    for (int t = threadIdx.x; t < nrow * 2 * nx * NV; t += blockDim.x) {
+      const int r = t / NV, c = t - r * NV;
+      Vout[((int64_t)2 * nx * y0 + r) * ldq + q0 + c] = nan4;
     }
   };
   // after a fault anywhere, later CTAs and launches only mark their outputs
   if (*reinterpret_cast<volatile unsigned int*>(&g_step_fault) != 0u) {
-    poison(g0);
+    poison();
     return;
   }
   const bool aligned = (smem_u32(win) & 127u) == 0 && (blockDim.x & 31) == 0;
@@ -993,8 +982,12 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   }
   if (!__syncthreads_and(aligned)) {
     if (threadIdx.x == 0) atomicOr(&g_step_fault, 2u);
-    poison(g0);
+    poison();
     return;
+  }
+  if (threadIdx.x == 0) {
+    for (int w = 0; w <= min(3, nrow + 1); ++w) issue_v(w);
+    for (int c = 0; c <= min(1, nrow - 1); ++c) issue_c(c);
   }
 
   ulonglong2 pc[2][2], pn[2][2];
@@ -1004,10 +997,11 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     dst[0][0] = own0 ? *reinterpret_cast<const ulonglong2*>(g) : zero2;
     dst[0][1] = own0 ? *reinterpret_cast<const ulonglong2*>(g + ldq) : zero2;
     const int x1 = site1(r);
-    const float4* g1p = Vprev + (2 * ((int64_t)y * nx + (x1 < 0 ? 0 : x1))) * ldq + q0 + v;
-    dst[1][0] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1p) : zero2;
-    dst[1][1] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1p + ldq) : zero2;
+    const float4* g1 = Vprev + (2 * ((int64_t)y * nx + (x1 < 0 ? 0 : x1))) * ldq + q0 + v;
+    dst[1][0] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1) : zero2;
+    dst[1][1] = x1 >= 0 ? *reinterpret_cast<const ulonglong2*>(g1 + ldq) : zero2;
   };
+  if (MODE == 1) load_prev(y0, rot, pc);
 
   const u64 half2 = 0x3F0000003F000000ull;  // (0.5f, 0.5f)
   // one lattice row; V_{m-1} of row y in `cur`, row y+1 loaded into `nxt`
@@ -1019,12 +1013,11 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     const int rot_next = next_rot(rot);
     if (MODE == 1 && q + 1 < nrow) load_prev(y + 1, rot_next, nxt);
     bool ok = true;
-    if (q == 0) ok = step_wait<HOOK>(vbar(0), vpar(0)) && step_wait<HOOK>(vbar(1), vpar(1));
+    if (q == 0) ok = step_wait<HOOK>(vbar(0), 0) && step_wait<HOOK>(vbar(1), 0);
     ok = ok && step_wait<HOOK>(vbar(q + 2), vpar(q + 2)) && step_wait<HOOK>(cbar(q), cpar(q));
     if (threadIdx.x == 0 && ok) {
       // window row y+3 into the slot of y-2 and coefficients of y+2 into the
-      // slot of y-1, once every warp has finished row y-1 (row 0 of a
-      // segment: every row of the previous one finished at its block barrier)
+      // slot of y-1, once every warp has finished row y-1 (row 0: fresh slots)
       if (q >= 1) ok = step_wait<HOOK>(dbar(q - 1), dpar(q - 1));
       if (ok) {
         if (q + 4 <= nrow + 1) issue_v(q + 4);
@@ -1035,10 +1028,10 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
       *fail_flag = 1;
       return false;
     }
-    const float4* wm = win + ((wb + q) % 5) * rowsz + v;
-    const float4* w0 = win + ((wb + q + 1) % 5) * rowsz + v;
-    const float4* wp = win + ((wb + q + 2) % 5) * rowsz + v;
-    const float2* cf_row = coef + ((cbs + q) % 3) * crow;
+    const float4* wm = win + (q % 5) * rowsz + v;
+    const float4* w0 = win + ((q + 1) % 5) * rowsz + v;
+    const float4* wp = win + ((q + 2) % 5) * rowsz + v;
+    const float2* cf_row = coef + (q % 3) * crow;
     const int x1 = site1(rot);
 
 #pragma unroll
@@ -1070,52 +1063,21 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     rot = rot_next;
     return true;
   };
-
-  for (int64_t g = g0; g < g1;) {
-    const int64_t ch = g / ny;
-    y0 = (int)(g - ch * ny);
-    y1 = (int)(g1 - g < (int64_t)(ny - y0) ? y0 + (g1 - g) : ny);
-    nrow = y1 - y0;
-    cb0 = ch * CB;
-    q0 = cb0 / 2;
-    yj_lo = ny;
-    yj_hi = -1;
-    {
-      const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
-      if (cmap.probe_p) {
-        yj_lo = 0;
-        yj_hi = ny - 1;
-      } else if (chi >= clo) {
-        yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
-        yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
-      }
-    }
+  for (int q = 0; q < nrow; q += 2) {
+    if (!row(q, pc, pn)) break;
+    if (q + 1 < nrow && !row(q + 1, pn, pc)) break;
+  }
+  __syncthreads();
+  if (*fail_flag) {
+    // every copy the CTA issued may still be in flight: wait (bounded) for
+    // the last fill of every slot before the shared memory is released
     if (threadIdx.x == 0) {
-      for (int w = 0; w <= min(3, nrow + 1); ++w) issue_v(w);
-      for (int c = 0; c <= min(1, nrow - 1); ++c) issue_c(c);
-    }
-    if (MODE == 1) load_prev(y0, rot, pc);
-    for (int q = 0; q < nrow; q += 2) {
-      if (!row(q, pc, pn)) break;
-      if (q + 1 < nrow && !row(q + 1, pn, pc)) break;
+      atomicOr(&g_step_fault, 1u);
+      for (int w = max(0, w_hi - 4); w <= w_hi; ++w) step_wait<HOOK>(vbar(w), vpar(w), 2);
+      for (int c = max(0, c_hi - 2); c <= c_hi; ++c) step_wait<HOOK>(cbar(c), cpar(c), 2);
     }
     __syncthreads();
-    if (*fail_flag) {
-      // every copy the CTA issued may still be in flight: wait (bounded) for
-      // the last fill of every slot before the shared memory is released
-      if (threadIdx.x == 0) {
-        atomicOr(&g_step_fault, 1u);
-        for (int w = max(0, w_hi - 4); w <= w_hi; ++w) step_wait<HOOK>(vbar(w), vpar(w), 2);
-        for (int c = max(0, c_hi - 2); c <= c_hi; ++c) step_wait<HOOK>(cbar(c), cpar(c), 2);
-      }
-      __syncthreads();
-      poison(g);
-      return;
-    }
-    wb += nrow + 2;
-    cbs += nrow;
-    rb += nrow;
-    g += nrow;
+    poison();
   }
 }
 
@@ -1124,9 +1086,8 @@ __global__ void __launch_bounds__(512, 1)
     cheb_step_f32_tma_kernel(const __grid_constant__ CUtensorMap tm, int nx, int ny, int64_t D, int64_t ldv,
                              int ylen, int brows, const float2* __restrict__ table, const float4* Vprev, float4* Vout,
                              ColMap cmap, double2* __restrict__ acc, const double* __restrict__ am,
-                             const double* __restrict__ ao, int m, int flat) {
-  f32_step_body_tma<CB, MODE, HOOK>(&tm, nx, ny, D, ldv, ylen, brows, flat, table, Vprev, Vout, cmap, acc, am, ao,
-                                    m);
+                             const double* __restrict__ ao, int m) {
+  f32_step_body_tma<CB, MODE, HOOK>(&tm, nx, ny, D, ldv, ylen, brows, table, Vprev, Vout, cmap, acc, am, ao, m);
 }
 
 // Batched TMA step: blockIdx.z selects the cell; the two slab tensor maps of
@@ -1139,7 +1100,7 @@ __global__ void __launch_bounds__(512, 1)
   const int z = blockIdx.z;
   const bool cur_b = MODE == 1 && (m & 1);
   float4* out = reinterpret_cast<float4*>(cur_b ? b.A[z] : b.B[z]);
-  f32_step_body_tma<CB, MODE>(maps + 2 * z + (cur_b ? 1 : 0), nx, ny, D, ldv, ylen, brows, 0,
+  f32_step_body_tma<CB, MODE>(maps + 2 * z + (cur_b ? 1 : 0), nx, ny, D, ldv, ylen, brows,
                               reinterpret_cast<const float2*>(b.table[z]), out, out,
                               ColMap{0, 0, 0, 0u, nullptr, nullptr}, b.acc[z], b.am[z], b.ao[z], m);
 }
@@ -1830,11 +1791,8 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
     auto fn = g_step_hook_armed ? (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, true> : cheb_step_f32_tma_kernel<CT, 1, true>)
                                 : (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, false>
                                              : cheb_step_f32_tma_kernel<CT, 1, false>);
-    // flat: one CTA per SM over the chunk-rows in order; else bands x chunks
-    const int64_t tot = (p.ldv / CB) * p.ny;
-    const dim3 g = p.flat ? dim3((unsigned)std::min<int64_t>(kSMs, tot)) : grid;
-    fn<<<g, p.nthreads, sm, s>>>(tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, (const float2*)table,
-                                 (const float4*)Vprev, (float4*)Vout, colmap(p, s0), acc, am, ao, m, p.flat);
+    fn<<<grid, p.nthreads, sm, s>>>(tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, (const float2*)table,
+                                    (const float4*)Vprev, (float4*)Vout, colmap(p, s0), acc, am, ao, m);
     return cudaGetLastError();
   }
   if (mode == 0)
@@ -1954,7 +1912,6 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request,
       break;
     }
   }
-  p.flat = 0;
   p.cb2 = 0;
   p.ylen2 = 0;
   p.smem2 = 0;
@@ -1971,12 +1928,6 @@ ChebPlan plan_cheb(int nx, int ny, int64_t width, int precision, int cb_request,
   int best_rows = ny;
   band_rows_candidates(ny, chunks, &best_rows, 1);
   p.ylen = band_rows > 0 ? std::min(band_rows, ny) : best_rows;
-  // TMA step (chunks of 8 or 16 columns): the flat split over one CTA per SM
-  // on request, and by default where every CTA gets at least a chunk's worth
-  // of rows (the wave model's bands otherwise)
-  p.flat = p.tma_rows > 0 && (band_rows == KPM_BAND_FLAT || (band_rows == 0 && chunks * ny >= (int64_t)kSMs * ny))
-               ? 1
-               : 0;
   if (precision == KPM_FP32) {
     // double step: widest chunk (<= cb) whose three rings fit; bands of at
     // least 4 rows (each band recomputes two halo rows of V_{m+1} and reads

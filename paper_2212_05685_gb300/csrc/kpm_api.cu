@@ -231,8 +231,7 @@ int plan_pass(kpm_ctx* ctx, const kpm_model* m, const kpm_opts* o, PassPlan* pp)
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64 && o->precision != KPM_DF64)
     return fail(ctx, KPM_EINVAL, "unknown precision");
   if (o->block_width < 0 || o->cols_per_block < 0) return fail(ctx, KPM_EINVAL, "negative block width");
-  if (o->band_rows < 0 && o->band_rows != KPM_BAND_FLAT)
-    return fail(ctx, KPM_EINVAL, "band_rows must be >= 0 or KPM_BAND_FLAT");
+  if (o->band_rows < 0) return fail(ctx, KPM_EINVAL, "negative band_rows");
   const int64_t D = 2 * (int64_t)m->nx * m->ny;
   pp->elem = o->precision == KPM_FP32 ? 8 : 16;
   if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return fail(ctx, KPM_EINVAL, "temperature must be finite and >= 0");
@@ -1587,15 +1586,14 @@ int kpm_autotune(kpm_ctx* ctx, const kpm_model* model, const kpm_opts* opts, con
       // band heights of the one-step kernels: the default (the wave model's
       // best), its next two, and one band per chunk (the double-step kernel
       // keeps its own bands)
-      int bands[6] = {0, 0, 0, 0, 0, 0};
+      int bands[4] = {0, 0, 0, 0};
       int nband = 1;
       if (!mode) {
-        if (pp.cheb.tma_rows > 0 && !pp.cheb.flat) bands[nband++] = KPM_BAND_FLAT;
         int cand[4];
         int nc = band_rows_candidates(model->ny, pp.cheb.ldv / pp.cheb.cb, cand, 3);
         cand[nc++] = model->ny;
         for (int k = 0; k < nc; ++k) {
-          bool seen = !pp.cheb.flat && cand[k] == pp.cheb.ylen;
+          bool seen = cand[k] == pp.cheb.ylen;
           for (int j = 1; j < nband; ++j) seen = seen || bands[j] == cand[k];
           if (!seen) bands[nband++] = cand[k];
         }

@@ -24,7 +24,6 @@ struct ChebPlan {
   int nthreads;
   size_t smem;     // dynamic shared memory per CTA
   int tma_rows;    // FP32 step: Nambu rows per TMA box of a window row (0: cp.async staging)
-  int flat;        // TMA step: chunk-rows split evenly over one CTA per SM (else ylen-row bands)
   // FP32 double-step kernel (two recursion steps per launch); cb2 = 0: not used
   int cb2;         // columns per CTA (divides cb)
   int ylen2;       // lattice rows per band

@@ -80,8 +80,7 @@ extern "C" int kpm_observables_noalloc(const kpm_model* m, const kpm_opts* o, co
   if (m->nx < 2 || m->ny < 2 || o->M < 1) return KPM_EINVAL;
   if (o->precision != KPM_FP32 && o->precision != KPM_FP64) return KPM_EINVAL;
   if ((o->flags & KPM_FLAG_PH_HALF) || o->probe_p) return KPM_EINVAL;  // the exact full pass only
-  if (o->block_width < 0 || o->cols_per_block < 0 || (o->band_rows < 0 && o->band_rows != KPM_BAND_FLAT))
-    return KPM_EINVAL;
+  if (o->block_width < 0 || o->cols_per_block < 0 || o->band_rows < 0) return KPM_EINVAL;
   if (o->site_begin != 0 || o->site_end != 0) return KPM_EINVAL;      // all sites
   if (!(o->temperature >= 0.0 && o->temperature < 1e300)) return KPM_EINVAL;
   int dev = 0;

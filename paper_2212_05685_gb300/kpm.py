@@ -27,7 +27,6 @@ KPM_DF64 = 2
 KPM_FLAG_DOUBLE_STEP = 1
 KPM_FLAG_PH_HALF = 2
 KPM_FLAG_KEEP_TAIL = 4
-KPM_BAND_FLAT = -1
 KPM_REGENERATE = -1
 
 
