@@ -869,7 +869,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // HOOK: the instantiation launched while a failure-path test hook is armed
 // (kpm_inject_lost_copy): its waits read the test's limit and one CTA may
 // skip a window copy; the production instantiation has neither
-template <int CB, int MODE, bool HOOK = false>
+template <int CB, int MODE, bool HOOK = false, bool PR = true>
 __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx, int ny, int64_t D, int64_t ldv,
                                                   int ylen, int brows, const float2* __restrict__ table,
                                                   const float4* Vprev, float4* Vout, ColMap cmap,
@@ -917,7 +917,7 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   int yj_lo = ny, yj_hi = -1;
   {
     const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
-    if (cmap.probe_p) {
+    if (PR && cmap.probe_p) {
       yj_lo = 0;
       yj_hi = ny - 1;
     } else if (chi >= clo) {
@@ -1056,8 +1056,12 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
       *reinterpret_cast<ulonglong2*>(g + ldq) = o1;
     }
 
-    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi)
-      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cmap, cb0, m, am[m], ao[m], acc);
+    if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi) {
+      // PR = false: unit vectors only (the probing items compiled out)
+      ColMap cu = cmap;
+      if (!PR) cu.probe_p = 0;
+      moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cu, cb0, m, am[m], ao[m], acc);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(dbar(q));
     rot = rot_next;
@@ -1081,13 +1085,13 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
   }
 }
 
-template <int CB, int MODE, bool HOOK = false>
+template <int CB, int MODE, bool HOOK = false, bool PR = true>
 __global__ void __launch_bounds__(512, 1)
     cheb_step_f32_tma_kernel(const __grid_constant__ CUtensorMap tm, int nx, int ny, int64_t D, int64_t ldv,
                              int ylen, int brows, const float2* __restrict__ table, const float4* Vprev, float4* Vout,
                              ColMap cmap, double2* __restrict__ acc, const double* __restrict__ am,
                              const double* __restrict__ ao, int m) {
-  f32_step_body_tma<CB, MODE, HOOK>(&tm, nx, ny, D, ldv, ylen, brows, table, Vprev, Vout, cmap, acc, am, ao, m);
+  f32_step_body_tma<CB, MODE, HOOK, PR>(&tm, nx, ny, D, ldv, ylen, brows, table, Vprev, Vout, cmap, acc, am, ao, m);
 }
 
 // Batched TMA step: blockIdx.z selects the cell; the two slab tensor maps of
@@ -1711,7 +1715,9 @@ cudaError_t set_smem_f32(int nx) {
   if (e != cudaSuccess || CB < 8) return e;
   constexpr int CT = CB >= 8 ? CB : 8;
   for (auto fn : {cheb_step_f32_tma_kernel<CT, 0, false>, cheb_step_f32_tma_kernel<CT, 1, false>,
-                  cheb_step_f32_tma_kernel<CT, 0, true>, cheb_step_f32_tma_kernel<CT, 1, true>}) {
+                  cheb_step_f32_tma_kernel<CT, 0, true>, cheb_step_f32_tma_kernel<CT, 1, true>,
+                  cheb_step_f32_tma_kernel<CT, 0, false, false>, cheb_step_f32_tma_kernel<CT, 1, false, false>,
+                  cheb_step_f32_tma_kernel<CT, 0, true, false>, cheb_step_f32_tma_kernel<CT, 1, true, false>}) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
     if (e != cudaSuccess) return e;
   }
@@ -1788,9 +1794,16 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
     if (e != cudaSuccess) return e;
     const size_t sm = p.smem + kTmaBarBytes;
     // the failure-path test instantiation only while a test hook is armed
-    auto fn = g_step_hook_armed ? (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, true> : cheb_step_f32_tma_kernel<CT, 1, true>)
-                                : (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, false>
-                                             : cheb_step_f32_tma_kernel<CT, 1, false>);
+    // and, for unit start vectors, the instantiation without the probing items
+    auto fn = p.probe_p > 0
+                  ? (g_step_hook_armed ? (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, true>
+                                                    : cheb_step_f32_tma_kernel<CT, 1, true>)
+                                       : (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, false>
+                                                    : cheb_step_f32_tma_kernel<CT, 1, false>))
+                  : (g_step_hook_armed ? (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, true, false>
+                                                    : cheb_step_f32_tma_kernel<CT, 1, true, false>)
+                                       : (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, false, false>
+                                                    : cheb_step_f32_tma_kernel<CT, 1, false, false>));
     fn<<<grid, p.nthreads, sm, s>>>(tm, p.nx, p.ny, p.D, p.ldv, p.ylen, p.tma_rows, (const float2*)table,
                                     (const float4*)Vprev, (float4*)Vout, colmap(p, s0), acc, am, ao, m);
     return cudaGetLastError();
