@@ -916,13 +916,14 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
 
   int yj_lo = ny, yj_hi = -1;
   {
-    const int64_t clo = cmap.s0 + cb0, chi = min(D >> cmap.js, cmap.s0 + cb0 + CB) - 1;
+    const int js = PR ? cmap.js : 0;
+    const int64_t clo = cmap.s0 + cb0, chi = min(D >> js, cmap.s0 + cb0 + CB) - 1;
     if (PR && cmap.probe_p) {
       yj_lo = 0;
       yj_hi = ny - 1;
     } else if (chi >= clo) {
-      yj_lo = (int)(((clo << cmap.js) >> 1) / nx);
-      yj_hi = (int)(((chi << cmap.js) >> 1) / nx);
+      yj_lo = (int)(((clo << js) >> 1) / nx);
+      yj_hi = (int)(((chi << js) >> 1) / nx);
     }
   }
 
@@ -1057,9 +1058,13 @@ __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx,
     }
 
     if (MODE == 1 && acc != nullptr && y >= yj_lo && y <= yj_hi) {
-      // PR = false: unit vectors only (the probing items compiled out)
+      // PR = false: unit vectors of the full pass only (the probing items and
+      // the half-pass column shift compiled out)
       ColMap cu = cmap;
-      if (!PR) cu.probe_p = 0;
+      if (!PR) {
+        cu.probe_p = 0;
+        cu.js = 0;
+      }
       moment_sums<CB>(wm - v, w0 - v, wp - v, nx, y, D, cu, cb0, m, am[m], ao[m], acc);
     }
     __syncwarp();
@@ -1794,8 +1799,9 @@ cudaError_t launch_f32(const ChebPlan& p, const void* table, const void* Vcur, c
     if (e != cudaSuccess) return e;
     const size_t sm = p.smem + kTmaBarBytes;
     // the failure-path test instantiation only while a test hook is armed
-    // and, for unit start vectors, the instantiation without the probing items
-    auto fn = p.probe_p > 0
+    // and, for the unit start vectors of a full pass, the instantiation
+    // without the probing items and the half-pass shift
+    auto fn = p.probe_p > 0 || p.js != 0
                   ? (g_step_hook_armed ? (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, true>
                                                     : cheb_step_f32_tma_kernel<CT, 1, true>)
                                        : (mode == 0 ? cheb_step_f32_tma_kernel<CT, 0, false>
