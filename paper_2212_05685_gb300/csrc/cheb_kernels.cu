@@ -868,7 +868,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // row, so that every warp does the same work averaged over a few rows.
 // HOOK: the instantiation launched while a failure-path test hook is armed
 // (kpm_inject_lost_copy): its waits read the test's limit and one CTA may
-// skip a window copy; the production instantiation has neither
+// skip a window copy; the production instantiation has neither.
+// PR = false: the instantiation for the unit start vectors of a full pass
+// (no probing colours, no half-pass column shift), whose moment sums compile
+// without those branches; probing and half passes run PR = true.  The results
+// are the same bits either way (same items, same arithmetic).
 template <int CB, int MODE, bool HOOK = false, bool PR = true>
 __device__ __forceinline__ void f32_step_body_tma(const CUtensorMap* tm, int nx, int ny, int64_t D, int64_t ldv,
                                                   int ylen, int brows, const float2* __restrict__ table,
