@@ -1,6 +1,7 @@
 """Host-side logic of the benchmark: the key that ties committed ncu counters
-to the kernel source (comments do not change it, code does), and the
-traffic lookup that scales a capture by columns and refuses a stale one."""
+to the kernel source (comments do not change it, code does), the traffic
+lookup that scales a capture by columns and refuses a stale one, and the
+reference arm's JSON line (the oracle on the host cores; rank 0 only)."""
 import json
 import os
 import sys
@@ -39,3 +40,33 @@ def test_traffic_lookup_scales_and_refuses_stale_records():
     # the benchmark reports the record only while the kernel source is the captured one
     current = bench.measured_traffic("cheb_step_fp32_100x100.json", bench.kernel_hash(), rec["ldv"])
     assert current == (rec["dram_bytes_per_launch"] if bench.kernel_hash() == key else None)
+
+
+def _run_reference(env_extra):
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                           "--warmup", "0", "--sample-cols", "1"], cwd=ROOT, env=env, capture_output=True,
+                          text=True, timeout=300)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the metric, the impl tag, its CPU-baseline record and a host-only e2e."""
+    r = _run_reference({"RANK": "0", "WORLD_SIZE": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
